@@ -1,0 +1,452 @@
+/*
+ * hv_oracle.c -- the parity oracle for the display-driven tile renderer.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file.  It shares no code, header
+ * or constant with the CUDA library and must never be reached from the
+ * product path.
+ *
+ * What it computes (HiVision, Sec. 3.2, Algorithm 1 and Algorithm 2), written
+ * as the plain definition on an integer grid:
+ *
+ *   grid      : 2^31 units per axis, coordinates in [-2^30, 2^30), y grows
+ *               southward, tile row 0 is north (Sec. 4: 256 x 256 px tiles
+ *               in a tile pyramid, Sec. 2.2: 4^z tiles at level z).
+ *   pixel     : at zoom z one pixel is ps = 2^(23-z) units wide (the paper's
+ *               resolution R_z, Algorithm 1 step 1), pixel (i, j) of tile
+ *               (z, tx, ty) has centre
+ *                   cx = -2^30 + tx*2^(31-z) + i*ps + ps/2   (same for y).
+ *   samples   : the centre and the four super-samples cx +- ps/4,
+ *               cy +- ps/4 (Algorithm 1, the four points P1..P4).
+ *   radius    : R = r16 * 2^(19-z) units, r16 = style radius in 1/16 px
+ *               (Algorithm 1 step 2, R = N * R_z).
+ *   covered   : C(s, R) = exists an object o with dist(o, s) <= R
+ *               (closed comparison, Algorithm 1 "distance <= R").
+ *   coverage  : v = number of the four super-samples with C (0..4, the
+ *               output range of Algorithm 1).  The paper evaluates the
+ *               super-samples against the single object nearest to the pixel
+ *               centre; the oracle uses the exact per-sample definition.
+ *   fill      : f(c) = exists a polygon Q whose own edges, over all of its
+ *               rings, cross the ray from c towards +x an odd number of
+ *               times (Algorithm 2, ray casting with per-polygon edge
+ *               counts; level edges never count).  An edge (a, b) crosses
+ *               when (a.y > c.y) != (b.y > c.y) and its crossing lies
+ *               strictly right of c.  The half-open straddle rule stands in
+ *               for the paper's IsLevel flag and its segment cutting (Sec. 3.1).
+ *
+ * The algorithm is deliberately data driven (the flow of Fig. 1-1): every
+ * object is visited once, the requested tiles it can touch are looked up,
+ * and the exact predicate is evaluated on every sample of a window that
+ * contains all samples within reach.  A sample outside the window is farther
+ * than R from the object, so the window only saves work; the result is the
+ * definition above.  All arithmetic is exact integer arithmetic (int64, and
+ * unsigned __int128 for the one product that needs 126 bits).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MODE_MASK 0
+#define OR_MODE_COVERAGE 1
+#define OR_MODE_RGBA 2
+
+/* per-pixel flag bits kept while splatting */
+#define F_SUB_NW 1u   /* (cx - q, cy - q) */
+#define F_SUB_NE 2u   /* (cx + q, cy - q) */
+#define F_SUB_SW 4u   /* (cx - q, cy + q) */
+#define F_SUB_SE 8u   /* (cx + q, cy + q) */
+#define F_CENTRE 16u
+#define F_FILL 32u
+
+#define TILE_PX 256
+#define GRID_HALF ((int64_t)1 << 30)
+
+static int64_t floordiv(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) q -= 1;
+    return q;
+}
+
+static int64_t clamp64(int64_t v, int64_t lo, int64_t hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+/* ---- exact predicates ------------------------------------------------- */
+
+/* |o - s|^2 <= R^2 for a point object. */
+static int point_within(int64_t ox, int64_t oy, int64_t sx, int64_t sy, int64_t R) {
+    int64_t dx = ox - sx, dy = oy - sy;
+    return dx * dx + dy * dy <= R * R;
+}
+
+/* distance from s to the closed segment [a, b] is <= R.
+ * With d = b - a, w = s - a, t = w.d, L = d.d:
+ *   t <= 0  -> nearest point is a,
+ *   t >= L  -> nearest point is b,
+ *   else    -> squared distance is (w x d)^2 / L, so compare (w x d)^2 <= R^2 L.
+ * A zero-length segment has t = 0 and falls into the first case. */
+static int segment_within(int64_t ax, int64_t ay, int64_t bx, int64_t by,
+                          int64_t sx, int64_t sy, int64_t R) {
+    int64_t dx = bx - ax, dy = by - ay;
+    int64_t wx = sx - ax, wy = sy - ay;
+    int64_t t = wx * dx + wy * dy;
+    int64_t L = dx * dx + dy * dy;
+    if (t <= 0) return wx * wx + wy * wy <= R * R;
+    if (t >= L) {
+        int64_t ex = sx - bx, ey = sy - by;
+        return ex * ex + ey * ey <= R * R;
+    }
+    int64_t cross = wx * dy - wy * dx;
+    unsigned __int128 c = (unsigned __int128)(cross < 0 ? -cross : cross);
+    unsigned __int128 lhs = c * c;
+    unsigned __int128 rhs = (unsigned __int128)(uint64_t)(R * R) * (unsigned __int128)(uint64_t)L;
+    return lhs <= rhs;
+}
+
+/* Does edge (a, b) cross the ray from c towards +x?  Half-open in y, strict
+ * in x.  With lo/hi the endpoints ordered by y, the crossing is right of c
+ * iff (hi.x - lo.x)(c.y - lo.y) - (c.x - lo.x)(hi.y - lo.y) > 0. */
+static int edge_crosses_right(int64_t ax, int64_t ay, int64_t bx, int64_t by,
+                              int64_t cx, int64_t cy) {
+    if ((ay > cy) == (by > cy)) return 0;
+    int64_t lox = ax, loy = ay, hix = bx, hiy = by;
+    if (ay > by) { lox = bx; loy = by; hix = ax; hiy = ay; }
+    int64_t num = (hix - lox) * (cy - loy) - (cx - lox) * (hiy - loy);
+    return num > 0;
+}
+
+/* ---- requested-tile lookup --------------------------------------------- */
+
+typedef struct { uint64_t key; uint32_t req; } tile_ref;
+
+static uint64_t tile_key(uint32_t z, uint32_t tx, uint32_t ty) {
+    return ((uint64_t)z << 48) | ((uint64_t)tx << 24) | (uint64_t)ty;
+}
+
+static int cmp_ref(const void* a, const void* b) {
+    const tile_ref* x = (const tile_ref*)a;
+    const tile_ref* y = (const tile_ref*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->req < y->req ? -1 : (x->req > y->req);
+}
+
+typedef struct {
+    const uint32_t *z, *x, *y, *r16;
+    uint64_t n;
+    tile_ref* refs;          /* sorted by key */
+    int64_t rmax[32];        /* largest R requested at each zoom, -1 if none */
+    uint8_t* flags;          /* n * 65536 per-pixel flag bytes */
+} req_table;
+
+static int64_t radius_units(uint32_t r16, uint32_t z) { return (int64_t)r16 << (19 - z); }
+
+static int table_init(req_table* t, const uint32_t* z, const uint32_t* x,
+                      const uint32_t* y, const uint32_t* r16, uint64_t n) {
+    t->z = z; t->x = x; t->y = y; t->r16 = r16; t->n = n;
+    for (int k = 0; k < 32; k++) t->rmax[k] = -1;
+    t->refs = (tile_ref*)malloc(sizeof(tile_ref) * (n ? n : 1));
+    t->flags = (uint8_t*)calloc(n ? n * TILE_PX * TILE_PX : 1, 1);
+    if (!t->refs || !t->flags) return -1;
+    for (uint64_t i = 0; i < n; i++) {
+        t->refs[i].key = tile_key(z[i], x[i], y[i]);
+        t->refs[i].req = (uint32_t)i;
+        int64_t R = radius_units(r16[i], z[i]);
+        if (R > t->rmax[z[i]]) t->rmax[z[i]] = R;
+    }
+    qsort(t->refs, n, sizeof(tile_ref), cmp_ref);
+    return 0;
+}
+
+static void table_free(req_table* t) { free(t->refs); free(t->flags); }
+
+/* first index in refs with key >= k */
+static uint64_t table_lower(const req_table* t, uint64_t k) {
+    uint64_t lo = 0, hi = t->n;
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (t->refs[mid].key < k) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+/* Tile column containing grid coordinate v at zoom z, clamped to the pyramid. */
+static int64_t tile_of(int64_t v, uint32_t z) {
+    int64_t span = (int64_t)1 << (31 - z);
+    return clamp64(floordiv(v + GRID_HALF, span), 0, ((int64_t)1 << z) - 1);
+}
+
+/* The object-kind specific work done on one requested tile. */
+typedef void (*splat_fn)(const void* obj, uint32_t z, int64_t X0, int64_t Y0,
+                         int64_t R, uint8_t* flags);
+
+/* Visit every requested tile whose area lies within the largest requested
+ * radius of the box [x0, x1] x [y0, y1] and call f on it. */
+static void for_each_request(const req_table* t, int64_t x0, int64_t y0, int64_t x1,
+                             int64_t y1, const void* obj, splat_fn f) {
+    for (uint32_t z = 0; z < 32; z++) {
+        int64_t E = t->rmax[z];
+        if (E < 0) continue;
+        if (x1 + E < -GRID_HALF || y1 + E < -GRID_HALF) continue;
+        if (x0 - E >= GRID_HALF || y0 - E >= GRID_HALF) continue;
+        int64_t tx0 = tile_of(x0 - E, z), tx1 = tile_of(x1 + E, z);
+        int64_t ty0 = tile_of(y0 - E, z), ty1 = tile_of(y1 + E, z);
+        int64_t span = (int64_t)1 << (31 - z);
+        for (int64_t tx = tx0; tx <= tx1; tx++) {
+            for (int64_t ty = ty0; ty <= ty1; ty++) {
+                uint64_t k = tile_key(z, (uint32_t)tx, (uint32_t)ty);
+                for (uint64_t i = table_lower(t, k); i < t->n && t->refs[i].key == k; i++) {
+                    uint32_t r = t->refs[i].req;
+                    int64_t R = radius_units(t->r16[r], z);
+                    f(obj, z, -GRID_HALF + tx * span, -GRID_HALF + ty * span, R,
+                      t->flags + (uint64_t)r * TILE_PX * TILE_PX);
+                }
+            }
+        }
+    }
+}
+
+/* Pixel index range [*lo, *hi] whose footprint comes within R of [v0, v1]. */
+static void pixel_window(int64_t v0, int64_t v1, int64_t R, int64_t origin, int64_t ps,
+                         int64_t* lo, int64_t* hi) {
+    *lo = clamp64(floordiv(v0 - R - origin, ps) - 1, 0, TILE_PX - 1);
+    *hi = clamp64(floordiv(v1 + R - origin, ps) + 1, 0, TILE_PX - 1);
+}
+
+/* ---- points ----------------------------------------------------------- */
+
+typedef struct { int64_t x, y; } pt_obj;
+
+static void splat_point(const void* obj, uint32_t z, int64_t X0, int64_t Y0, int64_t R,
+                        uint8_t* flags) {
+    const pt_obj* o = (const pt_obj*)obj;
+    int64_t ps = (int64_t)1 << (23 - z), q = ps / 4;
+    int64_t i0, i1, j0, j1;
+    pixel_window(o->x, o->x, R, X0, ps, &i0, &i1);
+    pixel_window(o->y, o->y, R, Y0, ps, &j0, &j1);
+    for (int64_t j = j0; j <= j1; j++) {
+        int64_t cy = Y0 + j * ps + ps / 2;
+        for (int64_t i = i0; i <= i1; i++) {
+            int64_t cx = X0 + i * ps + ps / 2;
+            uint8_t f = 0;
+            if (point_within(o->x, o->y, cx - q, cy - q, R)) f |= F_SUB_NW;
+            if (point_within(o->x, o->y, cx + q, cy - q, R)) f |= F_SUB_NE;
+            if (point_within(o->x, o->y, cx - q, cy + q, R)) f |= F_SUB_SW;
+            if (point_within(o->x, o->y, cx + q, cy + q, R)) f |= F_SUB_SE;
+            if (point_within(o->x, o->y, cx, cy, R)) f |= F_CENTRE;
+            flags[j * TILE_PX + i] |= f;
+        }
+    }
+}
+
+/* ---- segments (linestring pieces and polygon edges) ------------------- */
+
+typedef struct { int64_t ax, ay, bx, by; } seg_obj;
+
+static void splat_segment(const void* obj, uint32_t z, int64_t X0, int64_t Y0, int64_t R,
+                          uint8_t* flags) {
+    const seg_obj* s = (const seg_obj*)obj;
+    int64_t ps = (int64_t)1 << (23 - z), q = ps / 4;
+    int64_t x0 = s->ax < s->bx ? s->ax : s->bx, x1 = s->ax < s->bx ? s->bx : s->ax;
+    int64_t y0 = s->ay < s->by ? s->ay : s->by, y1 = s->ay < s->by ? s->by : s->ay;
+    int64_t i0, i1, j0, j1;
+    pixel_window(x0, x1, R, X0, ps, &i0, &i1);
+    pixel_window(y0, y1, R, Y0, ps, &j0, &j1);
+    for (int64_t j = j0; j <= j1; j++) {
+        int64_t cy = Y0 + j * ps + ps / 2;
+        for (int64_t i = i0; i <= i1; i++) {
+            int64_t cx = X0 + i * ps + ps / 2;
+            uint8_t f = 0;
+            if (segment_within(s->ax, s->ay, s->bx, s->by, cx - q, cy - q, R)) f |= F_SUB_NW;
+            if (segment_within(s->ax, s->ay, s->bx, s->by, cx + q, cy - q, R)) f |= F_SUB_NE;
+            if (segment_within(s->ax, s->ay, s->bx, s->by, cx - q, cy + q, R)) f |= F_SUB_SW;
+            if (segment_within(s->ax, s->ay, s->bx, s->by, cx + q, cy + q, R)) f |= F_SUB_SE;
+            if (segment_within(s->ax, s->ay, s->bx, s->by, cx, cy, R)) f |= F_CENTRE;
+            flags[j * TILE_PX + i] |= f;
+        }
+    }
+}
+
+/* ---- polygon fill ----------------------------------------------------- */
+
+typedef struct {
+    const int32_t* xy;        /* all vertices, interleaved x, y */
+    const uint64_t* ring_off; /* ring r = vertices [ring_off[r], ring_off[r+1]) */
+    uint64_t r0, r1;          /* this polygon's rings [r0, r1) */
+    int64_t x0, y0, x1, y1;   /* its bounding box */
+} poly_obj;
+
+static int polygon_parity(const poly_obj* p, int64_t cx, int64_t cy) {
+    int parity = 0;
+    for (uint64_t r = p->r0; r < p->r1; r++) {
+        uint64_t v0 = p->ring_off[r], v1 = p->ring_off[r + 1];
+        for (uint64_t v = v0; v < v1; v++) {
+            uint64_t w = (v + 1 < v1) ? v + 1 : v0; /* rings close implicitly */
+            if (edge_crosses_right(p->xy[2 * v], p->xy[2 * v + 1], p->xy[2 * w],
+                                   p->xy[2 * w + 1], cx, cy))
+                parity ^= 1;
+        }
+    }
+    return parity;
+}
+
+static void splat_fill(const void* obj, uint32_t z, int64_t X0, int64_t Y0, int64_t R,
+                       uint8_t* flags) {
+    (void)R;
+    const poly_obj* p = (const poly_obj*)obj;
+    int64_t ps = (int64_t)1 << (23 - z);
+    int64_t i0, i1, j0, j1;
+    /* a centre outside the polygon's box has even parity */
+    pixel_window(p->x0, p->x1, 0, X0, ps, &i0, &i1);
+    pixel_window(p->y0, p->y1, 0, Y0, ps, &j0, &j1);
+    for (int64_t j = j0; j <= j1; j++) {
+        int64_t cy = Y0 + j * ps + ps / 2;
+        for (int64_t i = i0; i <= i1; i++) {
+            int64_t cx = X0 + i * ps + ps / 2;
+            if (polygon_parity(p, cx, cy)) flags[j * TILE_PX + i] |= F_FILL;
+        }
+    }
+}
+
+/* ---- output encoding (Sec. 4.1 Render Tiles; zone array -> image) ----- */
+
+static uint32_t popcount4(uint32_t f) {
+    return (f & 1u) + ((f >> 1) & 1u) + ((f >> 2) & 1u) + ((f >> 3) & 1u);
+}
+
+uint64_t oracle_tile_bytes(int mode) {
+    if (mode == OR_MODE_MASK) return TILE_PX * TILE_PX / 8;
+    if (mode == OR_MODE_COVERAGE) return TILE_PX * TILE_PX;
+    return TILE_PX * TILE_PX * 4;
+}
+
+/* style: line colour r,g,b,(unused) then fill colour r,g,b,(unused). */
+static void encode(const uint8_t* flags, uint64_t n, int mode, const uint8_t* style,
+                   uint8_t* out) {
+    uint64_t tb = oracle_tile_bytes(mode);
+    for (uint64_t t = 0; t < n; t++) {
+        const uint8_t* fl = flags + t * TILE_PX * TILE_PX;
+        uint8_t* o = out + t * tb;
+        memset(o, 0, tb);
+        for (int j = 0; j < TILE_PX; j++) {
+            for (int i = 0; i < TILE_PX; i++) {
+                uint32_t f = fl[j * TILE_PX + i];
+                uint32_t v = popcount4(f);
+                uint32_t filled = (f & F_FILL) ? 1u : 0u;
+                if (mode == OR_MODE_MASK) {
+                    if ((f & F_CENTRE) || filled) {
+                        /* bit b of little-endian word w of row j is pixel 32w+b */
+                        int w = i / 32, b = i % 32;
+                        o[(j * 8 + w) * 4 + b / 8] |= (uint8_t)(1u << (b % 8));
+                    }
+                } else if (mode == OR_MODE_COVERAGE) {
+                    o[j * TILE_PX + i] = (uint8_t)(v | (filled << 3));
+                } else {
+                    uint8_t* px = o + 4 * (j * TILE_PX + i);
+                    uint32_t alpha = (255u * v + 2u) >> 2;
+                    if (filled) {
+                        for (int c = 0; c < 3; c++)
+                            px[c] = (uint8_t)((style[c] * alpha + style[4 + c] * (255u - alpha) + 127u) / 255u);
+                        px[3] = 255;
+                    } else if (v) {
+                        px[0] = style[0]; px[1] = style[1]; px[2] = style[2];
+                        px[3] = (uint8_t)alpha;
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* ---- entry points ----------------------------------------------------- */
+
+static int check_requests(const uint32_t* z, const uint32_t* x, const uint32_t* y,
+                          const uint32_t* r16, uint64_t n) {
+    for (uint64_t i = 0; i < n; i++) {
+        if (z[i] > 19) return -2;
+        if (x[i] >= (1u << z[i]) || y[i] >= (1u << z[i])) return -2;
+        if (r16[i] < 1 || r16[i] > 1024) return -2;
+    }
+    return 0;
+}
+
+static int check_coords(const int32_t* xy, uint64_t n) {
+    for (uint64_t i = 0; i < 2 * n; i++)
+        if (xy[i] < -(int32_t)(1 << 30) || xy[i] > (int32_t)((1u << 30) - 1)) return -2;
+    return 0;
+}
+
+/* Points: xy = n interleaved (x, y).  Returns 0, -1 (no memory) or -2 (range). */
+int oracle_render_points(const int32_t* xy, uint64_t n, const uint32_t* z, const uint32_t* x,
+                         const uint32_t* y, const uint32_t* r16, uint64_t n_req, int mode,
+                         const uint8_t* style, uint8_t* out) {
+    if (check_requests(z, x, y, r16, n_req) || check_coords(xy, n)) return -2;
+    req_table t;
+    if (table_init(&t, z, x, y, r16, n_req)) { table_free(&t); return -1; }
+    for (uint64_t k = 0; k < n; k++) {
+        pt_obj o = {xy[2 * k], xy[2 * k + 1]};
+        for_each_request(&t, o.x, o.y, o.x, o.y, &o, splat_point);
+    }
+    encode(t.flags, n_req, mode, style, out);
+    table_free(&t);
+    return 0;
+}
+
+/* Linestrings: line l has vertices [line_off[l], line_off[l+1]) and is drawn as
+ * its consecutive segments; a line with fewer than two vertices draws nothing. */
+int oracle_render_lines(const int32_t* xy, uint64_t n_vert, const uint64_t* line_off,
+                        uint64_t n_lines, const uint32_t* z, const uint32_t* x,
+                        const uint32_t* y, const uint32_t* r16, uint64_t n_req, int mode,
+                        const uint8_t* style, uint8_t* out) {
+    if (check_requests(z, x, y, r16, n_req) || check_coords(xy, n_vert)) return -2;
+    req_table t;
+    if (table_init(&t, z, x, y, r16, n_req)) { table_free(&t); return -1; }
+    for (uint64_t l = 0; l < n_lines; l++) {
+        for (uint64_t v = line_off[l]; v + 1 < line_off[l + 1]; v++) {
+            seg_obj s = {xy[2 * v], xy[2 * v + 1], xy[2 * v + 2], xy[2 * v + 3]};
+            int64_t x0 = s.ax < s.bx ? s.ax : s.bx, x1 = s.ax < s.bx ? s.bx : s.ax;
+            int64_t y0 = s.ay < s.by ? s.ay : s.by, y1 = s.ay < s.by ? s.by : s.ay;
+            for_each_request(&t, x0, y0, x1, y1, &s, splat_segment);
+        }
+    }
+    encode(t.flags, n_req, mode, style, out);
+    table_free(&t);
+    return 0;
+}
+
+/* Polygons: ring r has vertices [ring_off[r], ring_off[r+1]) and closes
+ * implicitly; polygon p owns rings [poly_ring_off[p], poly_ring_off[p+1])
+ * (outer ring and holes alike).  The outline uses the request's radius on
+ * every edge; the fill is decided at the pixel centre. */
+int oracle_render_polygons(const int32_t* xy, uint64_t n_vert, const uint64_t* ring_off,
+                           uint64_t n_rings, const uint64_t* poly_ring_off, uint64_t n_polys,
+                           const uint32_t* z, const uint32_t* x, const uint32_t* y,
+                           const uint32_t* r16, uint64_t n_req, int mode, const uint8_t* style,
+                           uint8_t* out) {
+    (void)n_rings;
+    if (check_requests(z, x, y, r16, n_req) || check_coords(xy, n_vert)) return -2;
+    req_table t;
+    if (table_init(&t, z, x, y, r16, n_req)) { table_free(&t); return -1; }
+    for (uint64_t p = 0; p < n_polys; p++) {
+        poly_obj P = {xy, ring_off, poly_ring_off[p], poly_ring_off[p + 1], 0, 0, 0, 0};
+        int first = 1;
+        for (uint64_t r = P.r0; r < P.r1; r++) {
+            uint64_t v0 = ring_off[r], v1 = ring_off[r + 1];
+            for (uint64_t v = v0; v < v1; v++) {
+                uint64_t w = (v + 1 < v1) ? v + 1 : v0;
+                seg_obj s = {xy[2 * v], xy[2 * v + 1], xy[2 * w], xy[2 * w + 1]};
+                int64_t x0 = s.ax < s.bx ? s.ax : s.bx, x1 = s.ax < s.bx ? s.bx : s.ax;
+                int64_t y0 = s.ay < s.by ? s.ay : s.by, y1 = s.ay < s.by ? s.by : s.ay;
+                for_each_request(&t, x0, y0, x1, y1, &s, splat_segment);
+                if (first) { P.x0 = x0; P.y0 = y0; P.x1 = x1; P.y1 = y1; first = 0; }
+                if (x0 < P.x0) P.x0 = x0;
+                if (y0 < P.y0) P.y0 = y0;
+                if (x1 > P.x1) P.x1 = x1;
+                if (y1 > P.y1) P.y1 = y1;
+            }
+        }
+        if (!first) for_each_request(&t, P.x0, P.y0, P.x1, P.y1, &P, splat_fill);
+    }
+    encode(t.flags, n_req, mode, style, out);
+    table_free(&t);
+    return 0;
+}
