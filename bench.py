@@ -1,0 +1,321 @@
+"""Benchmark: tiles/s of the display-driven tile renderer on one GB300.
+
+Workload (default): 100M clustered points (64-component Gaussian mixture +
+5% uniform noise, int32 grid), 10,000 density-weighted tiles at zoom 8-14,
+radius 2 px, RGBA output (HiVision Exp. 2 shape: 10,000 random tiles, no
+result cache).  A step renders the whole batch of tiles with one call of
+hv_render_tiles (device-resident requests and output).  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Multi-GPU (torchrun): every rank holds a replica of the layer and renders its
+own batch of tiles (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import gen  # noqa: E402
+
+WORKLOAD = {
+    "workload": "clustered points 100M (64-Gaussian mixture + 5% noise, int32 grid), "
+                "10,000 density-weighted 256x256 tiles at zoom 8-14, radius 2 px, RGBA",
+    "n_points": 100_000_000,
+    "tiles_per_step": 10_000,
+    "zoom": [8, 14],
+    "r16": 32,
+    "mode": "rgba",
+}
+METRIC = "tiles/sec (256² px) and p99 tile latency, learned vs R-tree index, 1 GB300"
+STYLE_T = (230, 40, 20, 0, 30, 90, 200, 0)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--points", type=int, default=WORKLOAD["n_points"])
+    ap.add_argument("--tiles", type=int, default=WORKLOAD["tiles_per_step"])
+    ap.add_argument("--cpu-sample-tiles", type=int, default=48)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--count-sample-tiles", type=int, default=200)
+    ap.add_argument("--profile-steps", action="store_true",
+                    help="only warm-up + steps, no baselines (for ncu launch lists)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while running (start/stop around the
+    timed region)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def workload(args, rank):
+    pts = gen.gmm_points(args.points, seed=2, k=64)
+    reqs = gen.density_tiles(pts, args.tiles, 8, 14, WORKLOAD["r16"], seed=102 + rank)
+    return pts, reqs
+
+
+def cpu_baseline(pts, reqs, n_sample):
+    """The oracle (single-threaded C, data driven) on a bounded sample of the
+    batch's tiles: one pass over all objects for n_sample tiles."""
+    import oracle
+    oracle.build()
+    sample = reqs[np.linspace(0, len(reqs) - 1, n_sample).astype(np.int64)]
+    t0 = time.perf_counter()
+    oracle.render_points(pts, sample, oracle.MODE_RGBA, STYLE_T)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt, "unit": "tiles/s", "cores": 1, "kind": "oracle",
+            "sample": "%d of the %d tiles (evenly spaced), all %d points, single-threaded C"
+                      % (n_sample, len(reqs), len(pts)), "seconds": dt}
+
+
+def run_reference(args):
+    """The oracle as the reference arm, on the host cores (rank 0 only)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    pts, reqs = workload(args, 0)
+    n_sample = 8
+    times = []
+    for step in range(args.warmup + args.steps):
+        sample = reqs[(np.arange(n_sample) * 997 + step * 13) % len(reqs)]
+        t0 = time.perf_counter()
+        oracle.render_points(pts, sample, oracle.MODE_RGBA, STYLE_T)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    value = n_sample * len(times) / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "impl": "reference",
+            "config": dict(WORKLOAD, sample_tiles_per_step=n_sample),
+            "cpu_baseline": {"value": value, "unit": "tiles/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d tiles per step of the %d-tile batch, all %d points"
+                                       % (n_sample, len(reqs), len(pts))},
+            "e2e": {"value": value, "unit": "tiles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def algorithmic_bytes_per_tile(hv, layer, reqs_dev_np, torch, n_sample):
+    """Unique bytes the early-exit traversal must read per tile (inner nodes x
+    512 B + visited leaves x 32 points x 8 B) plus the tile's output and its
+    request, from the library's instrumented visit log on a tile sample."""
+    idx = np.linspace(0, len(reqs_dev_np) - 1, n_sample).astype(np.int64)
+    sample = reqs_dev_np[idx]
+    log = torch.empty(1 << 27, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    d_req = torch.from_numpy(hv.make_requests(sample).view(np.uint8).copy()).cuda()
+    out = torch.empty((len(sample), hv.hv_tile_bytes(hv.HV_MODE_RGBA)), dtype=torch.uint8, device="cuda")
+    hv.hv_render_tiles_counted(layer, d_req, len(sample), hv.HV_MODE_RGBA, hv.HV_INDEX_RTREE,
+                               hv.make_style(), out, out.numel(), log, log.numel(), cnt)
+    torch.cuda.synchronize()
+    n = int(cnt.item())
+    if n > log.numel():
+        return None
+    keys = torch.unique(log[:n])
+    kind = (keys >> 35) & 7
+    nodes = int((kind == 0).sum().item())
+    leaves = int((kind == 1).sum().item())
+    read = nodes * 512 + leaves * 32 * 8
+    per_tile = read / len(sample) + hv.hv_tile_bytes(hv.HV_MODE_RGBA) + 16
+    return {"per_tile": per_tile, "read_per_tile": read / len(sample), "nodes_per_tile": nodes / len(sample),
+            "leaves_per_tile": leaves / len(sample), "sample_tiles": len(sample)}
+
+
+def run_gb300(args):
+    import torch
+    from paper_2005_12489_gb300 import hv
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    pts, reqs = workload(args, rank)
+    ctx = hv.hv_create(local)
+    layer = hv.hv_layer_load_points(ctx, pts)
+    hv.hv_layer_build_index(layer, hv.HV_INDEX_RTREE)
+    info = hv.hv_layer_info_get(layer)
+    mode = hv.HV_MODE_RGBA
+    tb = hv.hv_tile_bytes(mode)
+    n = len(reqs)
+    style = hv.make_style(STYLE_T[:3], STYLE_T[4:7])
+    d_req = torch.from_numpy(hv.make_requests(reqs).view(np.uint8).copy()).cuda()
+    d_out = torch.empty((n, tb), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    launches_per_step = hv.hv_render_launches(layer, hv.HV_INDEX_RTREE)
+
+    def step():
+        hv.hv_render_tiles(layer, d_req, n, mode, hv.HV_INDEX_RTREE, style, d_out, d_out.numel(), stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 255)            # L2 flush between steps (not timed)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms / 1000.0)
+    if args.profile_steps:
+        if rank == 0:
+            print(json.dumps({"profile_steps": True, "ms_per_step": ms}), flush=True)
+        return
+    # ---- extras measured on rank 0 only ----
+    line = None
+    if rank == 0:
+        peak, peak_kind = measured_peak_hbm()
+        alg = algorithmic_bytes_per_tile(hv, layer, reqs, torch, args.count_sample_tiles)
+        roof = None
+        if alg is not None:
+            achieved = alg["per_tile"] * n / (ms / 1000.0) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                    "kernel": "k_render", "alg_bytes_per_tile": alg["per_tile"],
+                    "alg_detail": alg}
+        e2e = None
+        if not args.no_e2e:
+            h_req = hv.make_requests(reqs)
+            h_out = torch.empty((n, tb), dtype=torch.uint8, pin_memory=True)
+            for _ in range(2):
+                hv.hv_render_tiles(layer, h_req, n, mode, hv.HV_INDEX_RTREE, style, h_out, h_out.numel(), stream)
+            k_e2e = max(3, min(args.steps, 10))
+            t1 = time.perf_counter()
+            for _ in range(k_e2e):
+                hv.hv_render_tiles(layer, h_req, n, mode, hv.HV_INDEX_RTREE, style, h_out, h_out.numel(), stream)
+            dt = (time.perf_counter() - t1) / k_e2e
+            e2e = {"value": n / dt, "unit": "tiles/s", "h2d_bytes_per_step": int(h_req.nbytes),
+                   "d2h_bytes_per_step": int(n * tb), "ms_per_step": 1000 * dt,
+                   "path": "hv_render_tiles with host requests and pinned host output"}
+        cpu = None if args.no_cpu_baseline else cpu_baseline(pts, reqs, args.cpu_sample_tiles)
+        line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+                "data": "synthetic",
+                "config": dict(WORKLOAD, index="packed Hilbert R-tree", l2="flushed between steps "
+                               "(512 MiB write); layer 800 MB and output 2.6 GB exceed L2",
+                               parallelism="replicas" if world > 1 else "single GPU"),
+                "pixel_queries_per_s": value * 65536,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+                "wall_s_timed_region": wall, "step_ms": step_ms,
+                "index_build_ms": info.build_ms, "tree_levels": info.tree_levels}
+        print(json.dumps(line), flush=True)
+    hv.hv_layer_free(layer)
+    hv.hv_destroy(ctx)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

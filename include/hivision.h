@@ -1,0 +1,254 @@
+/*
+ * hivision.h -- C ABI of the GB300 display-driven tile renderer.
+ *
+ * A reimplementation, for one GPU, of the per-pixel spatial-index query of
+ * HiVision (Ma et al., "HiVision: Rapid Visualization of Large-Scale Spatial
+ * Vector Data", arXiv 2005.12489): every pixel of a requested 256 x 256 tile
+ * is decided by index queries against the layer's objects instead of
+ * rasterising every object (Sec. 1, Sec. 2.3 display-driven computing).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid.      Coordinates are int32 units of a 2^31 x 2^31 Web-Mercator grid,
+ *            each in [-2^30, 2^30); y grows southward.  Zoom z is 0..19; at
+ *            zoom z there are 2^z x 2^z tiles (Sec. 2.2) of 256 x 256 pixels
+ *            (Sec. 4) and a pixel is 2^(23-z) units wide (resolution R_z of
+ *            Algorithm 1).  Pixel (i, j) of tile (z, x, y) has its centre at
+ *            (-2^30 + x*2^(31-z) + i*2^(23-z) + 2^(22-z), same for y, j);
+ *            row j = 0 is the north edge.
+ * Radius.    r16 is the style radius (points) or half-width (lines, polygon
+ *            outlines) in 1/16 px, 1..1024; R = r16 * 2^(19-z) units
+ *            (Algorithm 1: R = N * R_z).
+ * Samples.   A sample s is covered when some object lies within distance
+ *            <= R of it (closed; Algorithm 1).  COVERAGE and RGBA use the
+ *            four super-samples at the pixel centre +-(2^(21-z), 2^(21-z))
+ *            (Algorithm 1, P1..P4); MASK uses the pixel centre.
+ * Fill.      A polygon layer also fills the pixel centres that lie inside
+ *            some polygon: that polygon's own edges (all its rings) cross the
+ *            ray from the centre towards +x an odd number of times, an edge
+ *            (a, b) crossing when (a.y > c.y) != (b.y > c.y) and its crossing
+ *            lies strictly right of c (Algorithm 2; this half-open rule
+ *            stands in for the paper's IsLevel flag and segment cutting,
+ *            Sec. 3.1).  Polygons are tested one by one, so two overlapping
+ *            polygons both fill; rings of one polygon combine by parity.
+ * Results are exact integer decisions: identical, bit for bit, to the plain
+ * definition above.
+ *
+ * Ownership.  Input arrays are copied by the library; the caller keeps them.
+ * Handles belong to the library until their *_free / hv_destroy.  Output
+ * buffers belong to the caller.  Pointers documented as "host or device" are
+ * classified with cudaPointerGetAttributes.  A stream argument is a
+ * cudaStream_t passed as void* (NULL = the legacy default stream).
+ *
+ * Errors.  Every call returns an hv_status.  On failure nothing is written
+ * to caller-visible outputs unless stated, and hv_last_error() returns a
+ * message for the calling thread.
+ */
+#ifndef HIVISION_H
+#define HIVISION_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hv_status {
+    HV_OK = 0,
+    HV_EINVAL = 1,    /* bad argument: null pointer, wrong size, bad mode, state */
+    HV_ERANGE = 2,    /* coordinate outside the grid, z > 19, x or y >= 2^z,
+                         r16 outside 1..1024 */
+    HV_ENOMEM = 3,    /* device allocation failed or the context's budget is spent */
+    HV_ECUDA = 4,     /* a CUDA runtime call failed */
+    HV_ETIMEOUT = 5,  /* a bounded wait ran out */
+    HV_EBUSY = 6,     /* the server's queue is full; retry later */
+    HV_ESTATE = 7     /* call not valid in the object's current state */
+} hv_status;
+
+/* Output modes; bytes per tile in brackets. */
+enum {
+    HV_MODE_MASK = 0,     /* [8192] 1 bit per pixel: bit b of little-endian
+                             uint32 word w of row j is pixel (32w + b, j).
+                             Set when the centre is covered, or filled. */
+    HV_MODE_COVERAGE = 1, /* [65536] 1 byte per pixel, row-major: the number
+                             of covered super-samples 0..4, plus 8 when the
+                             centre is filled (polygon layers). */
+    HV_MODE_RGBA = 2      /* [262144] 4 bytes per pixel R, G, B, A, row-major.
+                             v = covered super-samples, a = (255 v + 2) >> 2;
+                             filled: rgb = (line*a + fill*(255 - a) + 127) / 255
+                             per channel, A = 255; else v > 0: (line rgb, a);
+                             else (0, 0, 0, 0).  Not premultiplied. */
+};
+
+enum { HV_LAYER_POINTS = 0, HV_LAYER_LINES = 1, HV_LAYER_POLYGONS = 2 };
+
+/* Index kinds (bit flags for hv_layer_build_index; one value for rendering). */
+enum { HV_INDEX_RTREE = 1, HV_INDEX_LEARNED = 2 };
+
+typedef struct hv_ctx hv_ctx;
+typedef struct hv_layer hv_layer;
+typedef struct hv_server hv_server;
+
+/* One tile request, 16 bytes. */
+typedef struct hv_tile_req {
+    uint32_t x, y;    /* tile column and row, < 2^z */
+    uint16_t r16;     /* radius or half-width in 1/16 px, 1..1024 */
+    uint8_t z;        /* zoom 0..19 */
+    uint8_t mode;     /* server only: HV_MODE_*; ignored by hv_render_tiles */
+    uint32_t layer;   /* server only: index into the server's layers */
+} hv_tile_req;
+
+/* Colours; the alpha bytes are reserved (alpha comes from coverage). */
+typedef struct hv_style {
+    uint8_t line_rgba[4];  /* points, lines, polygon outlines */
+    uint8_t fill_rgba[4];  /* polygon interiors */
+} hv_style;
+
+typedef struct hv_build_opts {
+    uint32_t learned_segments;   /* piecewise-linear pieces (0 = default 65536) */
+    uint32_t learned_hidden;     /* MLP hidden width, <= 32 (0 = default 16) */
+    uint32_t learned_steps;      /* training steps (0 = default 400) */
+    uint32_t learned_seed;       /* initialisation seed */
+    uint32_t max_error;          /* accept the learned index only if its
+                                    position error bound is <= this (0 = 4096) */
+    uint32_t reserved[3];
+} hv_build_opts;
+
+typedef struct hv_layer_info {
+    uint32_t kind;               /* HV_LAYER_* */
+    uint32_t indexes;            /* HV_INDEX_* bits built */
+    uint64_t n_objects;          /* points, segments or polygon edges */
+    uint64_t n_polygons;         /* polygon layers: polygons */
+    int32_t mbr[4];              /* minx, miny, maxx, maxy of the layer (empty: 0) */
+    uint32_t tree_levels;        /* inner levels of the object R-tree */
+    uint64_t tree_nodes;         /* inner nodes of the object R-tree */
+    uint64_t device_bytes;       /* device memory held by the layer */
+    int64_t learned_error;       /* learned index: max |predicted - true| position */
+    uint64_t learned_outliers;   /* learned index: objects kept in the side list */
+    double build_ms;             /* last index build, device time */
+    double train_ms;             /* learned-index training, device time */
+} hv_layer_info;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  mem_budget caps the device bytes
+ * the context may hold (layers, indexes, scratch); 0 = no cap. */
+int hv_create(hv_ctx** out, int device, uint64_t mem_budget);
+int hv_destroy(hv_ctx* ctx);
+/* Message of the calling thread's last failed call ("" if none). */
+const char* hv_last_error(void);
+/* Bytes currently held by the context on its device. */
+int hv_ctx_device_bytes(hv_ctx* ctx, uint64_t* out);
+
+/* ---- layers (Sec. 3.1 data organisation; Sec. 4.1 Register Vector Data) -- */
+
+/* Points: xy holds n interleaved (x, y) pairs, host or device memory. */
+int hv_layer_load_points(hv_ctx* ctx, const int32_t* xy, uint64_t n, hv_layer** out);
+
+/* Linestrings, split into their segments (Sec. 3.1: segments, not whole
+ * objects, are the index records).  xy: n_vert interleaved (x, y) pairs (host
+ * or device); line_off: n_lines + 1 non-decreasing offsets (host), line l =
+ * vertices [line_off[l], line_off[l+1]), line_off[n_lines] == n_vert.  A line
+ * with fewer than two vertices draws nothing. */
+int hv_layer_load_linestrings(hv_ctx* ctx, const int32_t* xy, uint64_t n_vert,
+                              const uint64_t* line_off, uint64_t n_lines, hv_layer** out);
+
+/* Polygons (Sec. 3.1, the multi-level index of edges and polygon MBRs).
+ * Ring r = vertices [ring_off[r], ring_off[r+1]) and closes implicitly (its
+ * last vertex joins its first); polygon p = rings
+ * [poly_ring_off[p], poly_ring_off[p+1]), outer ring and holes alike.
+ * Offsets are host arrays, non-decreasing, ending at n_vert and n_rings. */
+int hv_layer_load_polygons(hv_ctx* ctx, const int32_t* xy, uint64_t n_vert,
+                           const uint64_t* ring_off, uint64_t n_rings,
+                           const uint64_t* poly_ring_off, uint64_t n_polys, hv_layer** out);
+
+/* Build the indexes named by `kinds` (HV_INDEX_RTREE is always built).
+ * R-tree: objects sorted by the Hilbert key of their box centre, packed 32 to
+ * a leaf, inner nodes of 32 child boxes (replaces the paper's Boost R-trees,
+ * Sec. 3.1, Sec. 5).  Learned: a piecewise-linear + MLP model of position vs
+ * Hilbert key with a measured error bound, confirmed by exact search, with
+ * the R-tree as its fallback.  opts may be NULL.  Synchronous. */
+int hv_layer_build_index(hv_layer* layer, uint32_t kinds, const hv_build_opts* opts);
+
+int hv_layer_info_get(hv_layer* layer, hv_layer_info* out);
+int hv_layer_free(hv_layer* layer);
+
+/* Write / read a built layer (objects, R-tree, learned model) to / from a
+ * binary file with a version header (the paper keeps its indexes as files,
+ * Sec. 4).  Loading restores the device arrays without rebuilding. */
+int hv_layer_save(hv_layer* layer, const char* path);
+int hv_layer_load_file(hv_ctx* ctx, const char* path, hv_layer** out);
+
+/* ---- rendering (Algorithm 1 SIBV, Algorithm 2 SIBF, Sec. 4.1 Render Tiles) */
+
+/* Bytes of one tile in `mode` (0 for an unknown mode). */
+uint64_t hv_tile_bytes(int mode);
+
+/* Render n tiles of `layer` into `out` (n * hv_tile_bytes(mode) bytes, tile k
+ * at offset k * hv_tile_bytes(mode)), using index `index_kind`.
+ *
+ * reqs: host or device.  Host requests are checked first (HV_ERANGE, nothing
+ *   written).  Device requests are checked by the kernel: an invalid request
+ *   yields an all-zero tile and sets a sticky flag read by
+ *   hv_layer_take_status().
+ * out: host or device.  When reqs and out are both device memory the call is
+ *   asynchronous on `stream`.  Otherwise requests are staged and / or tiles
+ *   are rendered into device scratch and copied back, and the call returns
+ *   after the stream has synchronised.
+ * style: colours for HV_MODE_RGBA (may be NULL otherwise).
+ * Tiles that the layer cannot reach are written as zeros without index work
+ * (Sec. 4.1, Parse Tasks). */
+int hv_render_tiles(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode,
+                    int index_kind, const hv_style* style, void* out, uint64_t out_bytes,
+                    void* stream);
+
+/* Read and clear the layer's sticky device status (bit 0: an invalid device
+ * request was seen).  Synchronises `stream`. */
+int hv_layer_take_status(hv_layer* layer, void* stream, uint32_t* status);
+
+/* Instrumented hv_render_tiles for measurement (not for production use):
+ * the same tiles, plus a log of every index read.  All buffers are device
+ * memory.  Each inner-node, leaf or polygon read appends one int64
+ *   (tile << 38) | (kind << 35) | id
+ * with kind 0 = inner node (id = node number across levels, 512 B read),
+ * 1 = leaf (id = leaf number, 32 objects read), 2 / 3 = node / leaf of the
+ * polygon-box tree, 4 = a polygon whose edges were scanned (id = polygon).
+ * *log_count receives the number of reads (entries past log_cap are dropped).
+ * Used to count the unique bytes the early-exit traversal must read. */
+int hv_render_tiles_counted(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode,
+                            int index_kind, const hv_style* style, void* out, uint64_t out_bytes,
+                            int64_t* log, uint64_t log_cap, int64_t* log_count, void* stream);
+
+/* Number of kernels hv_render_tiles launches per call (for launch accounting). */
+int hv_render_launches(hv_layer* layer, int index_kind, uint32_t* launches);
+
+/* ---- serving (Sec. 4: MTVS task pool, IMMF, HPVE as one GPU loop) ------ */
+
+typedef struct hv_server_opts {
+    uint32_t max_batch;        /* tiles per launch (0 = 256) */
+    uint32_t queue_capacity;   /* pending requests before HV_EBUSY (0 = 65536) */
+    uint64_t scratch_bytes;    /* device bytes for tiles in flight (0 = 1 GiB) */
+    uint32_t index_kind;       /* HV_INDEX_* used for layers that have it */
+    uint32_t use_graphs;       /* capture launches into CUDA graphs */
+    hv_style style;
+} hv_server_opts;
+
+typedef struct hv_done {
+    uint64_t tag;              /* the tag given to hv_server_submit */
+    int32_t status;            /* HV_OK or an error code */
+    uint32_t bytes;            /* tile bytes written to `data` */
+    const uint8_t* data;       /* host pointer, valid until the next poll */
+    double t_submit_us, t_start_us, t_done_us;  /* host clock, microseconds */
+} hv_done;
+
+int hv_server_start(hv_ctx* ctx, hv_layer* const* layers, uint32_t n_layers,
+                    const hv_server_opts* opts, hv_server** out);
+int hv_server_submit(hv_server* srv, const hv_tile_req* req, uint64_t tag);
+int hv_server_poll(hv_server* srv, hv_done* out, uint32_t max, uint32_t* n_out);
+int hv_server_stop(hv_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIVISION_H */

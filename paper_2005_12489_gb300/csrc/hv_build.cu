@@ -1,0 +1,349 @@
+// Index build: Hilbert-packed R-trees on the device (replaces the Boost
+// R-trees RtreeP / RtreeL / RtreeE / RtreeMBR of HiVision Sec. 3.1).
+//
+// Objects are sorted by the 62-bit Hilbert key of their box centre, packed
+// 32 to a leaf, and every inner node stores the 32 boxes of its children as
+// SoA int32 so one warp reads a node with four coalesced 128-byte loads.
+#include <cub/device/device_radix_sort.cuh>
+
+#include "hv_device.cuh"
+#include "hv_internal.h"
+
+namespace hv {
+
+namespace {
+
+struct PointObj {
+    using T = int2;
+    __device__ static int4 box(int2 p) { return make_int4(p.x, p.y, p.x, p.y); }
+};
+struct SegObj {
+    using T = int4;
+    __device__ static int4 box(int4 s) {
+        return make_int4(min(s.x, s.z), min(s.y, s.w), max(s.x, s.z), max(s.y, s.w));
+    }
+};
+struct BoxObj {
+    using T = int4;
+    __device__ static int4 box(int4 b) { return b; }
+};
+
+template <class O>
+__global__ void k_keys(const typename O::T* obj, uint64_t n, uint64_t* keys, uint32_t* idx) {
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 b = O::box(obj[i]);
+    uint64_t k;
+    if (b.x > b.z) {
+        k = (1ull << 62) - 1;  // empty box: sorts last, never intersects
+    } else {
+        k = hilbert_key(mid32(b.x, b.z), mid32(b.y, b.w));
+    }
+    keys[i] = k;
+    idx[i] = (uint32_t)i;
+}
+
+template <class T>
+__global__ void k_gather(const T* src, const uint32_t* idx, uint64_t n, T* dst) {
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+
+__device__ __forceinline__ int4 warp_union(int4 b) {
+    return make_int4(__reduce_min_sync(kFull, b.x), __reduce_min_sync(kFull, b.y),
+                     __reduce_max_sync(kFull, b.z), __reduce_max_sync(kFull, b.w));
+}
+
+// Leaf boxes: one warp per leaf of 32 consecutive objects.
+template <class O>
+__global__ void k_leaf_boxes(const typename O::T* obj, uint64_t n, uint64_t n_leaf, int4* box) {
+    uint64_t leaf = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (leaf >= n_leaf) return;
+    uint64_t i = leaf * 32 + lane;
+    int4 b = i < n ? O::box(obj[i]) : make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
+    b = warp_union(b);
+    if (lane == 0) box[leaf] = b;
+}
+
+// One inner level: node k stores the boxes of children [32k, 32k+32) as SoA
+// and its own box is their union.
+__global__ void k_level(const int4* child_box, uint64_t n_child, uint64_t n_node, int32_t* nodes,
+                        int4* node_box) {
+    uint64_t k = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (k >= n_node) return;
+    uint64_t c = k * 32 + lane;
+    int4 b = c < n_child ? child_box[c] : make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
+    int32_t* nd = nodes + k * 128;
+    nd[lane] = b.x;
+    nd[32 + lane] = b.y;
+    nd[64 + lane] = b.z;
+    nd[96 + lane] = b.w;
+    b = warp_union(b);
+    if (lane == 0) node_box[k] = b;
+}
+
+uint32_t grid_for(uint64_t threads, uint32_t block) { return (uint32_t)((threads + block - 1) / block); }
+
+struct Tmp {
+    Ctx* c;
+    std::vector<std::pair<void*, uint64_t>> v;
+    explicit Tmp(Ctx* c_) : c(c_) {}
+    int get(void** p, uint64_t bytes) {
+        int rc = dev_alloc(c, p, bytes ? bytes : 16);
+        if (rc == HV_OK) v.push_back({*p, bytes ? bytes : 16});
+        return rc;
+    }
+    ~Tmp() {
+        for (auto& a : v) dev_free(c, a.first, a.second);
+    }
+};
+
+// Sort objects by Hilbert key; returns sorted objects (replacing *obj), the
+// sorted keys and optionally the permutation.
+template <class O>
+int sort_objects(Ctx* c, typename O::T** obj, uint64_t n, uint64_t** keys_out, uint32_t** perm_out) {
+    using T = typename O::T;
+    Tmp tmp(c);
+    uint64_t *k_in, *k_out;
+    uint32_t *i_in, *i_out;
+    HV_TRY(tmp.get((void**)&k_in, n * 8));
+    HV_TRY(tmp.get((void**)&i_in, n * 4));
+    HV_TRY(dev_alloc(c, (void**)&k_out, n * 8));
+    int rc = tmp.get((void**)&i_out, n * 4);
+    if (rc != HV_OK) { dev_free(c, k_out, n * 8); return rc; }
+    k_keys<O><<<grid_for(n, 256), 256>>>(*obj, n, k_in, i_in);
+    size_t temp_bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, k_in, k_out, i_in, i_out, (int64_t)n, 0, 62);
+    void* temp;
+    rc = tmp.get(&temp, temp_bytes);
+    if (rc != HV_OK) { dev_free(c, k_out, n * 8); return rc; }
+    cudaError_t e = cub::DeviceRadixSort::SortPairs(temp, temp_bytes, k_in, k_out, i_in, i_out,
+                                                    (int64_t)n, 0, 62);
+    if (e != cudaSuccess) {
+        dev_free(c, k_out, n * 8);
+        set_error("radix sort failed: %s", cudaGetErrorString(e));
+        return HV_ECUDA;
+    }
+    T* sorted;
+    rc = dev_alloc(c, (void**)&sorted, n * sizeof(T));
+    if (rc != HV_OK) { dev_free(c, k_out, n * 8); return rc; }
+    k_gather<T><<<grid_for(n, 256), 256>>>(*obj, i_out, n, sorted);
+    if (perm_out) {
+        uint32_t* perm;
+        rc = dev_alloc(c, (void**)&perm, n * 4);
+        if (rc != HV_OK) { dev_free(c, k_out, n * 8); dev_free(c, sorted, n * sizeof(T)); return rc; }
+        cudaMemcpyAsync(perm, i_out, n * 4, cudaMemcpyDeviceToDevice);
+        *perm_out = perm;
+    }
+    HV_CUDA(cudaGetLastError());
+    HV_CUDA(cudaDeviceSynchronize());
+    dev_free(c, *obj, n * sizeof(T));
+    *obj = sorted;
+    *keys_out = k_out;
+    return HV_OK;
+}
+
+// Build the inner levels over sorted objects.
+template <class O>
+int build_levels(Ctx* c, const typename O::T* obj, uint64_t n, Tree* t) {
+    *t = Tree();
+    t->view.n_obj = n;
+    if (n == 0) return HV_OK;
+    Tmp tmp(c);
+    uint64_t n_leaf = (n + 31) / 32;
+    // count nodes per level
+    uint64_t counts[kMaxLevels + 1] = {};
+    uint64_t below = n_leaf, total = 0;
+    int top = 0;
+    do {
+        top++;
+        if (top > kMaxLevels) { set_error("tree too deep"); return HV_EINVAL; }
+        counts[top] = (below + 31) / 32;
+        total += counts[top];
+        below = counts[top];
+    } while (below > 1);
+    int4 *box_a, *box_b;
+    HV_TRY(tmp.get((void**)&box_a, n_leaf * 16));
+    HV_TRY(tmp.get((void**)&box_b, ((n_leaf + 31) / 32) * 16 + 16));
+    HV_TRY(dev_alloc(c, (void**)&t->nodes, total * 512));
+    t->nodes_bytes = total * 512;
+    t->n_nodes = total;
+    k_leaf_boxes<O><<<grid_for(n_leaf * 32, 256), 256>>>(obj, n, n_leaf, box_a);
+    uint64_t off = 0, n_child = n_leaf;
+    for (int l = 1; l <= top; l++) {
+        t->view.level_off[l] = off;
+        t->view.level_n[l] = counts[l];
+        k_level<<<grid_for(counts[l] * 32, 256), 256>>>(box_a, n_child, counts[l],
+                                                        t->nodes + off * 128, box_b);
+        off += counts[l];
+        n_child = counts[l];
+        int4* s = box_a; box_a = box_b; box_b = s;
+    }
+    HV_CUDA(cudaGetLastError());
+    int4 root;
+    HV_CUDA(cudaMemcpy(&root, box_a, 16, cudaMemcpyDeviceToHost));
+    t->view.nodes = t->nodes;
+    t->view.top = top;
+    t->view.root_box = root;
+    return HV_OK;
+}
+
+// ---- polygon preparation ----------------------------------------------------
+
+__device__ __forceinline__ uint64_t upper_bound_u64(const uint64_t* a, uint64_t n, uint64_t v) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Edge v joins vertex v to the next vertex of its ring (rings close implicitly).
+__global__ void k_ring_edges(const int2* xy, uint64_t n_vert, const uint64_t* ring_off,
+                             uint64_t n_rings, int4* edges) {
+    uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (v >= n_vert) return;
+    uint64_t r = upper_bound_u64(ring_off, n_rings + 1, v) - 1;
+    uint64_t w = v + 1 < ring_off[r + 1] ? v + 1 : ring_off[r];
+    int2 a = xy[v], b = xy[w];
+    edges[v] = make_int4(a.x, a.y, b.x, b.y);
+}
+
+// Segment for vertex v of line l when v + 1 is still in the line.
+__global__ void k_line_segments(const int2* xy, uint64_t n_vert, const uint64_t* line_off,
+                                uint64_t n_lines, const uint64_t* seg_start, int4* segs) {
+    uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (v >= n_vert) return;
+    uint64_t l = upper_bound_u64(line_off, n_lines + 1, v) - 1;
+    if (v + 1 >= line_off[l + 1]) return;
+    int2 a = xy[v], b = xy[v + 1];
+    segs[seg_start[l] + (v - line_off[l])] = make_int4(a.x, a.y, b.x, b.y);
+}
+
+// Polygon boxes and edge offsets: one warp per polygon.
+__global__ void k_poly_boxes(const int4* edges, const uint64_t* ring_off, const uint64_t* poly_ring_off,
+                             uint64_t n_poly, uint64_t* edge_off, int4* boxes) {
+    uint64_t p = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (p >= n_poly) return;
+    uint64_t e0 = ring_off[poly_ring_off[p]], e1 = ring_off[poly_ring_off[p + 1]];
+    int4 b = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
+    for (uint64_t e = e0 + lane; e < e1; e += 32) {
+        int4 s = edges[e];
+        b.x = min(b.x, min(s.x, s.z));
+        b.y = min(b.y, min(s.y, s.w));
+        b.z = max(b.z, max(s.x, s.z));
+        b.w = max(b.w, max(s.y, s.w));
+    }
+    b = warp_union(b);
+    if (lane == 0) {
+        boxes[p] = b;
+        edge_off[p] = e0;
+        if (p + 1 == n_poly) edge_off[n_poly] = e1;
+    }
+}
+
+}  // namespace
+
+void free_tree(Ctx* c, Tree* t) {
+    if (t->nodes) dev_free(c, t->nodes, t->nodes_bytes);
+    *t = Tree();
+}
+
+int build_tree_points(Layer* L) {
+    Ctx* c = L->ctx;
+    if (L->n_obj) {
+        HV_TRY(sort_objects<PointObj>(c, (int2**)&L->obj, L->n_obj, &L->keys, nullptr));
+    }
+    HV_TRY(build_levels<PointObj>(c, (const int2*)L->obj, L->n_obj, &L->tree));
+    HV_CUDA(cudaDeviceSynchronize());
+    return HV_OK;
+}
+
+int build_tree_segments(Layer* L) {
+    Ctx* c = L->ctx;
+    if (L->n_obj) {
+        HV_TRY(sort_objects<SegObj>(c, (int4**)&L->obj, L->n_obj, &L->keys, nullptr));
+    }
+    HV_TRY(build_levels<SegObj>(c, (const int4*)L->obj, L->n_obj, &L->tree));
+    HV_CUDA(cudaDeviceSynchronize());
+    return HV_OK;
+}
+
+int build_tree_polygons(Layer* L) {
+    Ctx* c = L->ctx;
+    // the edge tree (outline): sorted copy of the polygon-order edges
+    if (L->n_obj) {
+        int4* copy;
+        HV_TRY(dev_alloc(c, (void**)&copy, L->n_obj * 16));
+        HV_CUDA(cudaMemcpy(copy, L->poly_edges, L->n_obj * 16, cudaMemcpyDeviceToDevice));
+        if (L->obj) dev_free(c, L->obj, L->obj_bytes);
+        L->obj = copy;
+        L->obj_bytes = L->n_obj * 16;
+        HV_TRY(sort_objects<SegObj>(c, (int4**)&L->obj, L->n_obj, &L->keys, nullptr));
+    }
+    HV_TRY(build_levels<SegObj>(c, (const int4*)L->obj, L->n_obj, &L->tree));
+    // the polygon-box tree (fill)
+    if (L->n_poly) {
+        HV_TRY(sort_objects<BoxObj>(c, &L->mbr_obj, L->n_poly, &L->mbr_keys, &L->mbr_ids));
+    }
+    HV_TRY(build_levels<BoxObj>(c, L->mbr_obj, L->n_poly, &L->mbr_tree));
+    HV_CUDA(cudaDeviceSynchronize());
+    return HV_OK;
+}
+
+// ---- A0: layer preparation on the device (used by hv_api.cu) ---------------
+
+int prepare_lines(Ctx* c, const int2* d_xy, uint64_t n_vert, const uint64_t* h_line_off,
+                  uint64_t n_lines, int4** segs_out, uint64_t* n_seg_out) {
+    std::vector<uint64_t> start(n_lines + 1, 0);
+    for (uint64_t l = 0; l < n_lines; l++) {
+        uint64_t nv = h_line_off[l + 1] - h_line_off[l];
+        start[l + 1] = start[l] + (nv >= 2 ? nv - 1 : 0);
+    }
+    uint64_t n_seg = start[n_lines];
+    *n_seg_out = n_seg;
+    *segs_out = nullptr;
+    if (n_seg == 0) return HV_OK;
+    Tmp tmp(c);
+    uint64_t *d_off, *d_start;
+    HV_TRY(tmp.get((void**)&d_off, (n_lines + 1) * 8));
+    HV_TRY(tmp.get((void**)&d_start, (n_lines + 1) * 8));
+    HV_CUDA(cudaMemcpy(d_off, h_line_off, (n_lines + 1) * 8, cudaMemcpyHostToDevice));
+    HV_CUDA(cudaMemcpy(d_start, start.data(), (n_lines + 1) * 8, cudaMemcpyHostToDevice));
+    HV_TRY(dev_alloc(c, (void**)segs_out, n_seg * 16));
+    k_line_segments<<<grid_for(n_vert, 256), 256>>>(d_xy, n_vert, d_off, n_lines, d_start, *segs_out);
+    HV_CUDA(cudaGetLastError());
+    HV_CUDA(cudaDeviceSynchronize());
+    return HV_OK;
+}
+
+int prepare_polygons(Ctx* c, const int2* d_xy, uint64_t n_vert, const uint64_t* h_ring_off,
+                     uint64_t n_rings, const uint64_t* h_poly_ring_off, uint64_t n_polys, Layer* L) {
+    Tmp tmp(c);
+    uint64_t *d_ro, *d_pro;
+    HV_TRY(tmp.get((void**)&d_ro, (n_rings + 1) * 8));
+    HV_TRY(tmp.get((void**)&d_pro, (n_polys + 1) * 8));
+    HV_CUDA(cudaMemcpy(d_ro, h_ring_off, (n_rings + 1) * 8, cudaMemcpyHostToDevice));
+    HV_CUDA(cudaMemcpy(d_pro, h_poly_ring_off, (n_polys + 1) * 8, cudaMemcpyHostToDevice));
+    L->n_obj = n_vert;
+    L->n_poly = n_polys;
+    HV_TRY(dev_alloc(c, (void**)&L->poly_edges, (n_vert ? n_vert : 1) * 16));
+    HV_TRY(dev_alloc(c, (void**)&L->poly_edge_off, (n_polys + 1) * 8));
+    HV_TRY(dev_alloc(c, (void**)&L->mbr_obj, (n_polys ? n_polys : 1) * 16));
+    if (n_vert) k_ring_edges<<<grid_for(n_vert, 256), 256>>>(d_xy, n_vert, d_ro, n_rings, L->poly_edges);
+    if (n_polys) {
+        k_poly_boxes<<<grid_for(n_polys * 32, 256), 256>>>(L->poly_edges, d_ro, d_pro, n_polys,
+                                                           L->poly_edge_off, L->mbr_obj);
+    } else {
+        HV_CUDA(cudaMemset(L->poly_edge_off, 0, 8));
+    }
+    HV_CUDA(cudaGetLastError());
+    HV_CUDA(cudaDeviceSynchronize());
+    return HV_OK;
+}
+
+}  // namespace hv

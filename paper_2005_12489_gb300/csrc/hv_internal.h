@@ -1,0 +1,152 @@
+// Internal host-side structures of libhivision (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hivision.h"
+
+namespace hv {
+
+constexpr int kFanout = 32;        // children per inner node, objects per leaf
+constexpr int kMaxLevels = 16;     // inner levels of a tree (32^16 >> 2^64)
+constexpr int kTile = 256;         // tile side in pixels (Sec. 4)
+
+void set_error(const char* fmt, ...);
+
+// Device memory accounting against the context's budget.
+struct Ctx {
+    int device = 0;
+    uint64_t budget = 0;     // 0 = unlimited
+    uint64_t held = 0;
+    std::mutex mu;
+    // render scratch (request copies, host-output staging), grown on demand
+    void* req_buf = nullptr;
+    uint64_t req_cap = 0;
+    void* out_buf = nullptr;
+    uint64_t out_cap = 0;
+    void* pinned_req = nullptr;   // pinned staging for host requests
+    uint64_t pinned_req_cap = 0;
+    std::mutex render_mu;         // serialises use of the scratch above
+};
+
+int dev_alloc(Ctx* c, void** p, uint64_t bytes);
+void dev_free(Ctx* c, void* p, uint64_t bytes);
+
+// A packed R-tree over n objects sorted by Hilbert key.  Inner nodes hold 32
+// child boxes as SoA int32 [minx x32][miny x32][maxx x32][maxy x32] (512 B).
+// Level 1 nodes hold leaf boxes (a leaf = 32 consecutive objects), level l
+// nodes hold the boxes of level l-1 nodes, the root is the single node of the
+// top level.  Nodes of all levels live in one array; level l starts at
+// level_off[l].
+struct TreeView {
+    const int32_t* nodes = nullptr;
+    uint64_t level_off[kMaxLevels + 1] = {};
+    uint64_t level_n[kMaxLevels + 1] = {};
+    int top = 0;                 // level of the root, 0 = empty tree
+    uint64_t n_obj = 0;
+    int4 root_box = {0, 0, -1, -1};
+};
+
+struct Tree {
+    TreeView view;
+    int32_t* nodes = nullptr;
+    uint64_t nodes_bytes = 0;
+    uint64_t n_nodes = 0;
+};
+
+// Learned position index over the sorted Hilbert keys of a tree's objects.
+struct LearnedView {
+    const uint64_t* keys = nullptr;     // sorted keys, n_obj
+    const float* seg_a = nullptr;       // per piece: slope, intercept (positions)
+    const float* seg_b = nullptr;
+    const uint64_t* seg_k0 = nullptr;   // first key of each piece
+    const uint32_t* radix = nullptr;    // top-bits table -> first piece
+    const uint16_t* mlp = nullptr;      // bf16 weights, packed (see hv_learned.cu)
+    uint32_t n_seg = 0;
+    uint32_t radix_bits = 0;
+    uint32_t hidden = 0;
+    int64_t eps = 0;                    // max position error of the model
+    int32_t halo = 0;                   // max half-extent of indexed objects
+    uint64_t n_obj = 0;
+    // objects whose extent exceeds `halo` are kept out of the key ranges and
+    // are found through their own small R-tree
+    TreeView outliers;
+    const void* outlier_obj = nullptr;
+    bool ready = false;
+};
+
+struct Learned {
+    LearnedView view;
+    std::vector<std::pair<void*, uint64_t>> allocs;
+    Tree outlier_tree;
+    double train_ms = 0;
+    uint64_t n_outliers = 0;
+};
+
+struct Layer {
+    Ctx* ctx = nullptr;
+    int kind = HV_LAYER_POINTS;
+    uint32_t indexes = 0;
+    // raw objects (input order) until the index is built, then sorted
+    uint64_t n_obj = 0;          // points, segments, or polygon edges
+    void* obj = nullptr;         // int2 points or int4 segments (sorted once built)
+    uint64_t obj_bytes = 0;
+    uint64_t* keys = nullptr;    // sorted Hilbert keys of obj (after build)
+    Tree tree;                   // R-tree over obj
+    // polygons
+    uint64_t n_poly = 0;
+    int4* poly_edges = nullptr;      // edges in polygon order (a.x, a.y, b.x, b.y)
+    uint64_t* poly_edge_off = nullptr;  // n_poly + 1
+    int4* mbr_obj = nullptr;         // polygon boxes, sorted by Hilbert key
+    uint32_t* mbr_ids = nullptr;     // polygon id of each sorted box
+    uint64_t* mbr_keys = nullptr;
+    Tree mbr_tree;
+    Learned learned;                 // over obj
+    Learned mbr_learned;             // over polygon boxes
+    int4 mbr = {0, 0, -1, -1};
+    uint32_t* status = nullptr;      // sticky device status word
+    double build_ms = 0;
+    std::vector<std::pair<void*, uint64_t>> extra;  // other allocations
+};
+
+// index build (hv_build.cu)
+int build_tree_points(Layer* L);
+int build_tree_segments(Layer* L);
+int build_tree_polygons(Layer* L);
+void free_tree(Ctx* c, Tree* t);
+// learned index (hv_learned.cu)
+int build_learned(Layer* L, const hv_build_opts* opts);
+void free_learned(Ctx* c, Learned* l);
+// render (hv_render.cu)
+struct RenderLog {
+    int64_t* log;
+    uint64_t cap;
+    int64_t* count;
+};
+int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int index_kind,
+                  const hv_style* style, uint8_t* d_out, cudaStream_t stream,
+                  const RenderLog* log = nullptr);
+uint32_t render_launch_count(Layer* L, int index_kind);
+
+}  // namespace hv
+
+#define HV_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            hv::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                          __LINE__);                                                    \
+            return HV_ECUDA;                                                            \
+        }                                                                               \
+    } while (0)
+
+#define HV_TRY(expr)             \
+    do {                         \
+        int rc_ = (expr);        \
+        if (rc_ != HV_OK) return rc_; \
+    } while (0)

@@ -1,0 +1,545 @@
+// Tile rendering: tile cull, warp-cooperative traversal with early exit,
+// exact predicates and the output encode, fused in one kernel.
+//
+//   HiVision Algorithm 1 (SIBV): a pixel's value is the number of its four
+//   super-samples within distance R of some object (points, segments,
+//   polygon edges); MASK mode decides the pixel centre only.
+//   HiVision Algorithm 2 (SIBF): a pixel centre is filled when, for some
+//   polygon whose box contains it, that polygon's edges cross the ray from
+//   the centre an odd number of times.
+//
+// Work decomposition.  One CTA (8 warps) renders a 256 x 16 pixel strip of
+// one tile.  The CTA first culls the R-tree against the strip's box expanded
+// by R, breadth first, into a frontier of at most kFCap nodes in shared
+// memory (the deepest level that fits).  Each warp then takes 8 x 4 pixel
+// blocks (one pixel per lane, up to four samples per lane): it tests the
+// frontier against the box of its still-undecided samples, descends the
+// intersecting subtrees depth first (ballot of the 32 child boxes decides
+// which children to visit), evaluates the exact predicate on the objects of
+// each visited leaf, shrinks the box as samples are decided, and stops as
+// soon as every sample of the block is covered.  Results go to a per-pixel
+// byte array in shared memory; the epilogue encodes the strip (MASK bits,
+// COVERAGE bytes or RGBA) with coalesced 16-byte stores.
+#include "hv_device.cuh"
+#include "hv_internal.h"
+
+namespace hv {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kStripRows = 16;
+constexpr int kStrips = kTile / kStripRows;
+constexpr int kBW = 8, kBH = 4;
+constexpr int kBlocksX = kTile / kBW;
+constexpr int kBlocks = kBlocksX * (kStripRows / kBH);
+constexpr int kFCap = 512;
+
+// result bits per pixel
+constexpr uint32_t kResCentre = 16u, kResFill = 32u;
+
+struct TreeArg {
+    const int32_t* nodes;
+    uint64_t level_off[kMaxLevels + 1];
+    int top;
+    uint64_t n_obj;
+    int4 root_box;
+};
+
+struct Params {
+    const hv_tile_req* reqs;
+    uint32_t n;
+    int mode;
+    int kind;
+    uchar4 line;
+    uchar4 fill;
+    uint8_t* out;
+    uint32_t tile_bytes;
+    TreeArg tree;               // points, segments or polygon edges
+    const void* obj;
+    TreeArg mtree;              // polygon boxes (polygon layers)
+    const int4* mbr_obj;
+    const uint32_t* mbr_ids;
+    const int4* poly_edges;
+    const uint64_t* poly_edge_off;
+    uint32_t* status;
+    // instrumentation (NULL in normal use): every node, leaf and polygon read
+    // is appended as (tile << 38 | kind << 35 | id)
+    unsigned long long* log;
+    unsigned long long log_cap;
+    unsigned long long* log_n;
+};
+
+// kinds of logged reads
+constexpr uint32_t kLogNode = 0, kLogLeaf = 1, kLogPolyNode = 2, kLogPolyLeaf = 3, kLogPoly = 4;
+
+__device__ __forceinline__ void log_read(const Params& p, uint32_t kind, uint64_t id, int lane) {
+    if (p.log != nullptr && lane == 0) {
+        unsigned long long k = atomicAdd(p.log_n, 1ull);
+        if (k < p.log_cap)
+            p.log[k] = ((unsigned long long)(blockIdx.x / kStrips) << 38) | ((unsigned long long)kind << 35) | id;
+    }
+}
+
+struct Smem {
+    uint8_t res[kStripRows * kTile];
+    int4 fbox[2][kFCap];
+    uint32_t fid[2][kFCap];
+    const int32_t* lvl_base[kMaxLevels + 1];
+    uint32_t stk_node[kWarps][kMaxLevels + 1];
+    uint32_t stk_mask[kWarps][kMaxLevels + 1];
+    int f_count, f_level, f_buf, next_count, next_block;
+};
+
+// Per-lane state of one pixel block.
+struct Lane {
+    int32_t cx, cy, off;       // pixel centre, super-sample offset (0 in MASK mode)
+    int32_t R;
+    int64_t R2;
+    uint32_t und;              // undecided samples (bit k: sample k)
+    int32_t qx0, qy0, qx1, qy1;  // query box: undecided samples +- R (warp-uniform)
+    bool done;                 // warp-uniform: every sample decided
+};
+
+__device__ __forceinline__ int32_t sample_x(const Lane& s, int k) { return s.cx + ((k & 1) ? s.off : -s.off); }
+__device__ __forceinline__ int32_t sample_y(const Lane& s, int k) { return s.cy + ((k & 2) ? s.off : -s.off); }
+
+// Recompute the warp's query box from its undecided samples.
+__device__ __forceinline__ void refresh(Lane& s, int32_t expand) {
+    int32_t x0 = kEmptyLo, y0 = kEmptyLo, x1 = kEmptyHi, y1 = kEmptyHi;
+    if (s.und) {
+        x0 = (s.und & 5u) ? s.cx - s.off : s.cx + s.off;
+        x1 = (s.und & 10u) ? s.cx + s.off : s.cx - s.off;
+        y0 = (s.und & 3u) ? s.cy - s.off : s.cy + s.off;
+        y1 = (s.und & 12u) ? s.cy + s.off : s.cy - s.off;
+    }
+    s.done = __ballot_sync(kFull, s.und != 0) == 0;
+    x0 = __reduce_min_sync(kFull, x0);
+    y0 = __reduce_min_sync(kFull, y0);
+    x1 = __reduce_max_sync(kFull, x1);
+    y1 = __reduce_max_sync(kFull, y1);
+    s.qx0 = x0 - expand;
+    s.qy0 = y0 - expand;
+    s.qx1 = x1 + expand;
+    s.qy1 = y1 + expand;
+}
+
+// ---- leaf visitors -----------------------------------------------------------
+
+struct PointLeaf {
+    static constexpr bool kFill = false;
+    __device__ static void visit(const Params& p, uint32_t leaf, Lane& s, int lane) {
+        uint64_t i = (uint64_t)leaf * 32 + lane;
+        log_read(p, kLogLeaf, leaf, lane);
+        int2 o = make_int2(kEmptyHi, kEmptyHi);
+        if (i < p.tree.n_obj) o = __ldg((const int2*)p.obj + i);
+        bool hit = o.x >= s.qx0 && o.x <= s.qx1 && o.y >= s.qy0 && o.y <= s.qy1;
+        uint32_t m = __ballot_sync(kFull, hit);
+        if (!m) return;
+        while (m) {
+            int k = __ffs(m) - 1;
+            m &= m - 1;
+            int32_t ox = __shfl_sync(kFull, o.x, k), oy = __shfl_sync(kFull, o.y, k);
+            uint32_t u = s.und;
+            while (u) {
+                int b = __ffs(u) - 1;
+                u &= u - 1;
+                if (point_within(ox, oy, sample_x(s, b), sample_y(s, b), s.R2)) s.und &= ~(1u << b);
+            }
+        }
+        refresh(s, s.R);
+    }
+};
+
+struct SegLeaf {
+    static constexpr bool kFill = false;
+    __device__ static void visit(const Params& p, uint32_t leaf, Lane& s, int lane) {
+        uint64_t i = (uint64_t)leaf * 32 + lane;
+        log_read(p, kLogLeaf, leaf, lane);
+        int4 o = make_int4(kEmptyHi, kEmptyHi, kEmptyHi, kEmptyHi);
+        if (i < p.tree.n_obj) o = __ldg((const int4*)p.obj + i);
+        bool hit = min(o.x, o.z) <= s.qx1 && max(o.x, o.z) >= s.qx0 && min(o.y, o.w) <= s.qy1 &&
+                   max(o.y, o.w) >= s.qy0;
+        uint32_t m = __ballot_sync(kFull, hit);
+        if (!m) return;
+        while (m) {
+            int k = __ffs(m) - 1;
+            m &= m - 1;
+            int32_t ax = __shfl_sync(kFull, o.x, k), ay = __shfl_sync(kFull, o.y, k);
+            int32_t bx = __shfl_sync(kFull, o.z, k), by = __shfl_sync(kFull, o.w, k);
+            uint32_t u = s.und;
+            while (u) {
+                int b = __ffs(u) - 1;
+                u &= u - 1;
+                if (segment_within(ax, ay, bx, by, sample_x(s, b), sample_y(s, b), s.R2))
+                    s.und &= ~(1u << b);
+            }
+        }
+        refresh(s, s.R);
+    }
+};
+
+// Polygon boxes: a leaf holds 32 polygon boxes; for each box that contains an
+// unfilled pixel centre, count that polygon's own edges crossing the ray.
+struct FillLeaf {
+    static constexpr bool kFill = true;
+    __device__ static void visit(const Params& p, uint32_t leaf, Lane& s, int lane) {
+        uint64_t i = (uint64_t)leaf * 32 + lane;
+        log_read(p, kLogPolyLeaf, leaf, lane);
+        int4 b = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
+        uint32_t id = 0;
+        if (i < p.mtree.n_obj) {
+            b = __ldg(p.mbr_obj + i);
+            id = __ldg(p.mbr_ids + i);
+        }
+        uint32_t m = __ballot_sync(kFull, box_hit(b, s.qx0, s.qy0, s.qx1, s.qy1));
+        if (!m) return;
+        while (m) {
+            int k = __ffs(m) - 1;
+            m &= m - 1;
+            int32_t bx0 = __shfl_sync(kFull, b.x, k), by0 = __shfl_sync(kFull, b.y, k);
+            int32_t bx1 = __shfl_sync(kFull, b.z, k), by1 = __shfl_sync(kFull, b.w, k);
+            uint32_t pid = __shfl_sync(kFull, id, k);
+            bool active = s.und && s.cx >= bx0 && s.cx <= bx1 && s.cy >= by0 && s.cy <= by1;
+            if (__ballot_sync(kFull, active) == 0) continue;
+            log_read(p, kLogPoly, pid, lane);
+            uint64_t e0 = __ldg(p.poly_edge_off + pid), e1 = __ldg(p.poly_edge_off + pid + 1);
+            uint32_t parity = 0;
+            for (uint64_t base = e0; base < e1; base += 32) {
+                int4 e = make_int4(0, 0, 0, 0);
+                if (base + lane < e1) e = __ldg(p.poly_edges + base + lane);
+                int cnt = (e1 - base) < 32 ? (int)(e1 - base) : 32;
+                for (int j = 0; j < cnt; j++) {
+                    int32_t ax = __shfl_sync(kFull, e.x, j), ay = __shfl_sync(kFull, e.y, j);
+                    int32_t cx2 = __shfl_sync(kFull, e.z, j), cy2 = __shfl_sync(kFull, e.w, j);
+                    if (active && edge_crosses_right(ax, ay, cx2, cy2, s.cx, s.cy)) parity ^= 1u;
+                }
+            }
+            if (active && parity) s.und = 0;
+        }
+        refresh(s, 0);
+    }
+};
+
+// Ballot of the children of node `node` at level `lvl` whose boxes meet the
+// warp's query box.
+__device__ __forceinline__ uint32_t child_hits(const Params& p, bool fill, const int32_t* base,
+                                               const Lane& s, int lane) {
+    if (p.log != nullptr)
+        log_read(p, fill ? kLogPolyNode : kLogNode,
+                 (uint64_t)(base - (fill ? p.mtree.nodes : p.tree.nodes)) >> 7, lane);
+    int4 b = make_int4(__ldg(base + lane), __ldg(base + 32 + lane), __ldg(base + 64 + lane),
+                       __ldg(base + 96 + lane));
+    return __ballot_sync(kFull, box_hit(b, s.qx0, s.qy0, s.qx1, s.qy1));
+}
+
+// Depth-first descent from node `node` at level `level` (>= 1).
+template <class V>
+__device__ void descend(const Params& p, Smem& sm, int level, uint32_t node, Lane& s, int lane, int warp) {
+    uint32_t* stk_node = sm.stk_node[warp];
+    uint32_t* stk_mask = sm.stk_mask[warp];
+    int lvl = level;
+    uint32_t m0 = child_hits(p, V::kFill, sm.lvl_base[lvl] + (uint64_t)node * 128, s, lane);
+    stk_node[lvl] = node;
+    stk_mask[lvl] = m0;
+    __syncwarp();
+    while (true) {
+        uint32_t m = stk_mask[lvl];
+        if (m == 0) {
+            if (lvl == level) break;
+            lvl++;
+            continue;
+        }
+        int c = __ffs(m) - 1;
+        uint32_t child = stk_node[lvl] * 32u + (uint32_t)c;
+        __syncwarp();
+        stk_mask[lvl] = m & (m - 1);
+        __syncwarp();
+        if (lvl == 1) {
+            V::visit(p, child, s, lane);
+            if (s.done) return;
+        } else {
+            lvl--;
+            uint32_t hm = child_hits(p, V::kFill, sm.lvl_base[lvl] + (uint64_t)child * 128, s, lane);
+            stk_node[lvl] = child;
+            stk_mask[lvl] = hm;
+            __syncwarp();
+        }
+    }
+}
+
+// Breadth-first cull of a tree against a box into the shared frontier.
+__device__ void cull(const Params& p, const TreeArg& t, bool fill, Smem& sm, int32_t x0, int32_t y0,
+                     int32_t x1, int32_t y1, int tid) {
+    int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int l = 0; l <= kMaxLevels; l++)
+        if (tid == l) sm.lvl_base[l] = (l >= 1 && l <= t.top) ? t.nodes + t.level_off[l] * 128 : nullptr;
+    if (tid == 0) {
+        sm.f_buf = 0;
+        sm.f_level = t.top;
+        sm.f_count = 0;
+        if (t.top > 0 && t.root_box.x <= x1 && t.root_box.z >= x0 && t.root_box.y <= y1 &&
+            t.root_box.w >= y0) {
+            sm.fid[0][0] = 0;
+            sm.fbox[0][0] = t.root_box;
+            sm.f_count = 1;
+        }
+    }
+    __syncthreads();
+    while (sm.f_level >= 1 && sm.f_count > 0) {
+        int cur = sm.f_buf, lvl = sm.f_level, cnt = sm.f_count;
+        if (tid == 0) sm.next_count = 0;
+        __syncthreads();
+        const int32_t* base = sm.lvl_base[lvl];
+        for (int e = warp; e < cnt; e += kWarps) {
+            uint32_t node = sm.fid[cur][e];
+            const int32_t* nd = base + (uint64_t)node * 128;
+            if (p.log != nullptr)
+                log_read(p, fill ? kLogPolyNode : kLogNode, (uint64_t)(nd - t.nodes) >> 7, lane);
+            int4 b = make_int4(__ldg(nd + lane), __ldg(nd + 32 + lane), __ldg(nd + 64 + lane),
+                               __ldg(nd + 96 + lane));
+            bool hit = box_hit(b, x0, y0, x1, y1);
+            uint32_t m = __ballot_sync(kFull, hit);
+            int pos = 0;
+            if (lane == 0 && m) pos = atomicAdd(&sm.next_count, __popc(m));
+            pos = __shfl_sync(kFull, pos, 0);
+            if (hit) {
+                int slot = pos + __popc(m & ((1u << lane) - 1u));
+                if (slot < kFCap) {
+                    sm.fid[cur ^ 1][slot] = node * 32u + (uint32_t)lane;
+                    sm.fbox[cur ^ 1][slot] = b;
+                }
+            }
+        }
+        __syncthreads();
+        int nc = sm.next_count;
+        __syncthreads();
+        if (nc > kFCap) break;  // keep the current (coarser) frontier
+        if (tid == 0) {
+            sm.f_buf = cur ^ 1;
+            sm.f_count = nc;
+            sm.f_level = lvl - 1;
+        }
+        __syncthreads();
+    }
+}
+
+// Process every pixel block of the strip against the current frontier.
+template <class V>
+__device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, int strip, int z,
+                            int32_t R, bool mask_mode, int tid) {
+    int lane = tid & 31, warp = tid >> 5;
+    int32_t ps = 1 << (23 - z);
+    const int f_count = sm.f_count, f_level = sm.f_level, fb = sm.f_buf;
+    while (true) {
+        int blk = 0;
+        if (lane == 0) blk = atomicAdd(&sm.next_block, 1);
+        blk = __shfl_sync(kFull, blk, 0);
+        if (blk >= kBlocks) break;
+        int bx = blk % kBlocksX, by = blk / kBlocksX;
+        int i = bx * kBW + (lane & 7);
+        int jl = by * kBH + (lane >> 3);
+        int j = strip * kStripRows + jl;
+        Lane s;
+        s.cx = X0 + i * ps + (ps >> 1);
+        s.cy = Y0 + j * ps + (ps >> 1);
+        s.R = R;
+        s.R2 = (int64_t)R * R;
+        if (V::kFill) {
+            s.off = 0;
+            s.und = 1u;
+        } else {
+            s.off = mask_mode ? 0 : (ps >> 2);
+            s.und = mask_mode ? 1u : 15u;
+        }
+        uint32_t und0 = s.und;
+        refresh(s, V::kFill ? 0 : R);
+        for (int c0 = 0; c0 < f_count && !s.done; c0 += 32) {
+            int e = c0 + lane;
+            bool hit = e < f_count && box_hit(sm.fbox[fb][e], s.qx0, s.qy0, s.qx1, s.qy1);
+            uint32_t m = __ballot_sync(kFull, hit);
+            while (m && !s.done) {
+                int k = __ffs(m) - 1;
+                m &= m - 1;
+                uint32_t id = sm.fid[fb][c0 + k];
+                if (f_level == 0) {
+                    V::visit(p, id, s, lane);
+                } else {
+                    descend<V>(p, sm, f_level, id, s, lane, warp);
+                }
+                if (m) {
+                    // drop frontier entries the shrunken box no longer meets
+                    bool still = e < f_count && ((m >> lane) & 1u) &&
+                                 box_hit(sm.fbox[fb][e], s.qx0, s.qy0, s.qx1, s.qy1);
+                    m = __ballot_sync(kFull, still);
+                }
+            }
+        }
+        uint32_t covered = und0 & ~s.und;
+        uint8_t r = sm.res[jl * kTile + i];
+        if (V::kFill) {
+            if (covered) r |= kResFill;
+        } else if (mask_mode) {
+            if (covered) r |= kResCentre;
+        } else {
+            r |= (uint8_t)covered;
+        }
+        sm.res[jl * kTile + i] = r;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_render(const Params p) {
+    __shared__ Smem sm;
+    const int tid = threadIdx.x;
+    const uint32_t tile = blockIdx.x / kStrips;
+    const int strip = blockIdx.x % kStrips;
+    if (tile >= p.n) return;
+    hv_tile_req q = p.reqs[tile];
+    bool ok = q.z <= 19 && q.x < (1u << q.z) && q.y < (1u << q.z) && q.r16 >= 1 && q.r16 <= 1024;
+    for (int k = tid; k < kStripRows * kTile / 4; k += kThreads) ((uint32_t*)sm.res)[k] = 0u;
+    if (!ok) {
+        if (tid == 0 && strip == 0) atomicOr(p.status, 1u);
+    }
+    __syncthreads();
+    const bool mask_mode = p.mode == HV_MODE_MASK;
+    if (ok) {
+        const int z = q.z;
+        const int32_t ps = 1 << (23 - z);
+        const int32_t X0 = (int32_t)(-(int64_t)kGridHalf + (int64_t)q.x * ((int64_t)1 << (31 - z)));
+        const int32_t Y0 = (int32_t)(-(int64_t)kGridHalf + (int64_t)q.y * ((int64_t)1 << (31 - z)));
+        const int32_t R = (int32_t)q.r16 << (19 - z);
+        const int32_t off = mask_mode ? 0 : (ps >> 2);
+        // strip sample box
+        const int32_t sx0 = X0 + (ps >> 1) - off, sx1 = X0 + (kTile - 1) * ps + (ps >> 1) + off;
+        const int32_t sy0 = Y0 + strip * kStripRows * ps + (ps >> 1) - off;
+        const int32_t sy1 = Y0 + (strip * kStripRows + kStripRows - 1) * ps + (ps >> 1) + off;
+        // Algorithm 1 over points / segments / polygon edges
+        cull(p, p.tree, false, sm, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
+        if (tid == 0) sm.next_block = 0;
+        __syncthreads();
+        if (sm.f_count > 0) {
+            if (p.kind == HV_LAYER_POINTS)
+                blocks_pass<PointLeaf>(p, sm, X0, Y0, strip, z, R, mask_mode, tid);
+            else
+                blocks_pass<SegLeaf>(p, sm, X0, Y0, strip, z, R, mask_mode, tid);
+        }
+        __syncthreads();
+        // Algorithm 2 over polygon boxes and edges
+        if (p.kind == HV_LAYER_POLYGONS) {
+            const int32_t cx0 = X0 + (ps >> 1), cx1 = X0 + (kTile - 1) * ps + (ps >> 1);
+            const int32_t cy0 = Y0 + strip * kStripRows * ps + (ps >> 1);
+            const int32_t cy1 = Y0 + (strip * kStripRows + kStripRows - 1) * ps + (ps >> 1);
+            cull(p, p.mtree, true, sm, cx0, cy0, cx1, cy1, tid);
+            if (tid == 0) sm.next_block = 0;
+            __syncthreads();
+            if (sm.f_count > 0) blocks_pass<FillLeaf>(p, sm, X0, Y0, strip, z, 0, mask_mode, tid);
+            __syncthreads();
+        }
+    }
+    // ---- encode the strip (Sec. 4.1 Render Tiles) ----
+    uint8_t* out = p.out + (uint64_t)tile * p.tile_bytes;
+    if (p.mode == HV_MODE_MASK) {
+        // 16 rows x 8 words; word w of row j = pixels 32w .. 32w+31
+        if (tid < kStripRows * 8) {
+            int jl = tid >> 3, w = tid & 7;
+            uint32_t word = 0;
+            for (int b = 0; b < 32; b++)
+                if (sm.res[jl * kTile + 32 * w + b] & (kResCentre | kResFill)) word |= 1u << b;
+            ((uint32_t*)out)[(strip * kStripRows + jl) * 8 + w] = word;
+        }
+    } else if (p.mode == HV_MODE_COVERAGE) {
+        // 4 KB contiguous: one uint4 (16 pixels) per thread
+        const uint8_t* r = sm.res + tid * 16;
+        uint32_t w4[4];
+        for (int k = 0; k < 4; k++) {
+            uint32_t v = 0;
+            for (int b = 0; b < 4; b++) {
+                uint32_t f = r[4 * k + b];
+                uint32_t c = __popc(f & 15u) | ((f & kResFill) ? 8u : 0u);
+                v |= c << (8 * b);
+            }
+            w4[k] = v;
+        }
+        ((uint4*)(out + (uint64_t)strip * kStripRows * kTile))[tid] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+    } else {
+        // 16 KB contiguous: four rounds of one uint4 (4 pixels) per thread
+        uint4* o4 = (uint4*)(out + (uint64_t)strip * kStripRows * kTile * 4);
+        for (int it = 0; it < 4; it++) {
+            int px = (it * kThreads + tid) * 4;
+            uint32_t w[4];
+            for (int b = 0; b < 4; b++) {
+                uint32_t f = sm.res[px + b];
+                uint32_t v = __popc(f & 15u);
+                uint32_t a = (255u * v + 2u) >> 2;
+                uint32_t rgba = 0;
+                if (f & kResFill) {
+                    uint32_t r = (p.line.x * a + p.fill.x * (255u - a) + 127u) / 255u;
+                    uint32_t g = (p.line.y * a + p.fill.y * (255u - a) + 127u) / 255u;
+                    uint32_t bl = (p.line.z * a + p.fill.z * (255u - a) + 127u) / 255u;
+                    rgba = r | (g << 8) | (bl << 16) | (255u << 24);
+                } else if (v) {
+                    rgba = (uint32_t)p.line.x | ((uint32_t)p.line.y << 8) | ((uint32_t)p.line.z << 16) | (a << 24);
+                }
+                w[b] = rgba;
+            }
+            o4[it * kThreads + tid] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+TreeArg tree_arg(const TreeView& v) {
+    TreeArg a;
+    a.nodes = v.nodes;
+    for (int l = 0; l <= kMaxLevels; l++) a.level_off[l] = v.level_off[l];
+    a.top = v.top;
+    a.n_obj = v.n_obj;
+    a.root_box = v.root_box;
+    return a;
+}
+
+}  // namespace
+
+uint32_t render_launch_count(Layer*, int) { return 1; }
+
+int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int index_kind,
+                  const hv_style* style, uint8_t* d_out, cudaStream_t stream, const RenderLog* log) {
+    (void)index_kind;
+    if (n == 0) return HV_OK;
+    Params p;
+    memset(&p, 0, sizeof(p));
+    p.reqs = d_reqs;
+    p.n = n;
+    p.mode = mode;
+    p.kind = L->kind;
+    if (style) {
+        p.line = make_uchar4(style->line_rgba[0], style->line_rgba[1], style->line_rgba[2], 0);
+        p.fill = make_uchar4(style->fill_rgba[0], style->fill_rgba[1], style->fill_rgba[2], 0);
+    }
+    p.out = d_out;
+    p.tile_bytes = (uint32_t)hv_tile_bytes(mode);
+    p.tree = tree_arg(L->tree.view);
+    p.obj = L->obj;
+    p.mtree = tree_arg(L->mbr_tree.view);
+    p.mbr_obj = L->mbr_obj;
+    p.mbr_ids = L->mbr_ids;
+    p.poly_edges = L->poly_edges;
+    p.poly_edge_off = L->poly_edge_off;
+    p.status = L->status;
+    if (log) {
+        p.log = (unsigned long long*)log->log;
+        p.log_cap = log->cap;
+        p.log_n = (unsigned long long*)log->count;
+    }
+    uint64_t grid = (uint64_t)n * kStrips;
+    if (grid > 0x7fffffffull) {
+        set_error("too many tiles in one call");
+        return HV_EINVAL;
+    }
+    k_render<<<(unsigned)grid, kThreads, 0, stream>>>(p);
+    HV_CUDA(cudaGetLastError());
+    return HV_OK;
+}
+
+}  // namespace hv

@@ -1,0 +1,309 @@
+"""ctypes binding of libhivision (argument marshalling only).
+
+Every function has the name of the C entry point it calls (include/hivision.h)
+and raises ``HVError`` when the call returns a non-zero status.  Array
+arguments may be numpy arrays (host memory), torch tensors (host or device;
+their ``data_ptr()`` is passed) or raw integer addresses.  Streams may be a
+``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or None.
+
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_2005_12489_gb300.build``); there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhivision.so")
+
+HV_OK, HV_EINVAL, HV_ERANGE, HV_ENOMEM, HV_ECUDA, HV_ETIMEOUT, HV_EBUSY, HV_ESTATE = range(8)
+STATUS_NAMES = ["HV_OK", "HV_EINVAL", "HV_ERANGE", "HV_ENOMEM", "HV_ECUDA", "HV_ETIMEOUT",
+                "HV_EBUSY", "HV_ESTATE"]
+HV_MODE_MASK, HV_MODE_COVERAGE, HV_MODE_RGBA = 0, 1, 2
+HV_LAYER_POINTS, HV_LAYER_LINES, HV_LAYER_POLYGONS = 0, 1, 2
+HV_INDEX_RTREE, HV_INDEX_LEARNED = 1, 2
+
+REQ_DTYPE = np.dtype([("x", "<u4"), ("y", "<u4"), ("r16", "<u2"), ("z", "u1"), ("mode", "u1"),
+                      ("layer", "<u4")])
+assert REQ_DTYPE.itemsize == 16
+
+
+class HVError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+        self.status = status
+
+
+class hv_style(ctypes.Structure):
+    _fields_ = [("line_rgba", ctypes.c_uint8 * 4), ("fill_rgba", ctypes.c_uint8 * 4)]
+
+
+class hv_build_opts(ctypes.Structure):
+    _fields_ = [("learned_segments", ctypes.c_uint32), ("learned_hidden", ctypes.c_uint32),
+                ("learned_steps", ctypes.c_uint32), ("learned_seed", ctypes.c_uint32),
+                ("max_error", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+
+
+class hv_layer_info(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("indexes", ctypes.c_uint32),
+                ("n_objects", ctypes.c_uint64), ("n_polygons", ctypes.c_uint64),
+                ("mbr", ctypes.c_int32 * 4), ("tree_levels", ctypes.c_uint32),
+                ("tree_nodes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("learned_error", ctypes.c_int64), ("learned_outliers", ctypes.c_uint64),
+                ("build_ms", ctypes.c_double), ("train_ms", ctypes.c_double)]
+
+
+class hv_server_opts(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("queue_capacity", ctypes.c_uint32),
+                ("scratch_bytes", ctypes.c_uint64), ("index_kind", ctypes.c_uint32),
+                ("use_graphs", ctypes.c_uint32), ("style", hv_style)]
+
+
+class hv_done(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("bytes", ctypes.c_uint32),
+                ("data", ctypes.c_void_p), ("t_submit_us", ctypes.c_double),
+                ("t_start_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+_lib = None
+P = ctypes.c_void_p
+U64 = ctypes.c_uint64
+U32 = ctypes.c_uint32
+I32 = ctypes.c_int
+
+SIGNATURES = {
+    "hv_create": [ctypes.POINTER(P), I32, U64],
+    "hv_destroy": [P],
+    "hv_last_error": [],
+    "hv_ctx_device_bytes": [P, ctypes.POINTER(U64)],
+    "hv_layer_load_points": [P, P, U64, ctypes.POINTER(P)],
+    "hv_layer_load_linestrings": [P, P, U64, P, U64, ctypes.POINTER(P)],
+    "hv_layer_load_polygons": [P, P, U64, P, U64, P, U64, ctypes.POINTER(P)],
+    "hv_layer_build_index": [P, U32, P],
+    "hv_layer_info_get": [P, ctypes.POINTER(hv_layer_info)],
+    "hv_layer_free": [P],
+    "hv_layer_save": [P, ctypes.c_char_p],
+    "hv_layer_load_file": [P, ctypes.c_char_p, ctypes.POINTER(P)],
+    "hv_tile_bytes": [I32],
+    "hv_render_tiles": [P, P, U32, I32, I32, P, P, U64, P],
+    "hv_layer_take_status": [P, P, ctypes.POINTER(U32)],
+    "hv_render_tiles_counted": [P, P, U32, I32, I32, P, P, U64, P, U64, P, P],
+    "hv_render_launches": [P, I32, ctypes.POINTER(U32)],
+    "hv_server_start": [P, P, U32, ctypes.POINTER(hv_server_opts), ctypes.POINTER(P)],
+    "hv_server_submit": [P, P, U64],
+    "hv_server_poll": [P, ctypes.POINTER(hv_done), U32, ctypes.POINTER(U32)],
+    "hv_server_stop": [P],
+}
+
+
+def lib():
+    """Load libhivision.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libhivision.so is not built (%s); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.hv_last_error.restype = ctypes.c_char_p
+        L.hv_tile_bytes.restype = U64
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != HV_OK:
+        raise HVError(rc, lib().hv_last_error().decode(errors="replace"))
+
+
+def ptr(a):
+    """Address of a numpy array, torch tensor, ctypes object or int."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "array must be contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        return a.data_ptr()
+    return ctypes.addressof(a)
+
+
+def stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def hv_last_error():
+    return lib().hv_last_error().decode(errors="replace")
+
+
+def hv_tile_bytes(mode):
+    return int(lib().hv_tile_bytes(mode))
+
+
+def hv_create(device=0, mem_budget=0):
+    out = P()
+    _check(lib().hv_create(ctypes.byref(out), device, mem_budget))
+    return out.value
+
+
+def hv_destroy(ctx):
+    _check(lib().hv_destroy(ctx))
+
+
+def hv_ctx_device_bytes(ctx):
+    out = U64()
+    _check(lib().hv_ctx_device_bytes(ctx, ctypes.byref(out)))
+    return out.value
+
+
+def _i32xy(xy):
+    if isinstance(xy, np.ndarray):
+        return np.ascontiguousarray(xy, dtype=np.int32)
+    return xy
+
+
+def _u64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint64))
+
+
+def hv_layer_load_points(ctx, xy, n=None):
+    xy = _i32xy(xy)
+    n = (xy.shape[0] if n is None else n)
+    out = P()
+    _check(lib().hv_layer_load_points(ctx, ptr(xy), n, ctypes.byref(out)))
+    return out.value
+
+
+def hv_layer_load_linestrings(ctx, xy, line_off):
+    xy = _i32xy(xy)
+    off = _u64(line_off)
+    out = P()
+    _check(lib().hv_layer_load_linestrings(ctx, ptr(xy), int(off[-1]), ptr(off), off.shape[0] - 1,
+                                           ctypes.byref(out)))
+    return out.value
+
+
+def hv_layer_load_polygons(ctx, xy, ring_off, poly_ring_off):
+    xy = _i32xy(xy)
+    ro, po = _u64(ring_off), _u64(poly_ring_off)
+    out = P()
+    _check(lib().hv_layer_load_polygons(ctx, ptr(xy), int(ro[-1]), ptr(ro), ro.shape[0] - 1, ptr(po),
+                                        po.shape[0] - 1, ctypes.byref(out)))
+    return out.value
+
+
+def hv_layer_build_index(layer, kinds=HV_INDEX_RTREE, opts=None):
+    _check(lib().hv_layer_build_index(layer, kinds, ctypes.byref(opts) if opts is not None else None))
+
+
+def hv_layer_info_get(layer):
+    info = hv_layer_info()
+    _check(lib().hv_layer_info_get(layer, ctypes.byref(info)))
+    return info
+
+
+def hv_layer_free(layer):
+    _check(lib().hv_layer_free(layer))
+
+
+def hv_layer_save(layer, path):
+    _check(lib().hv_layer_save(layer, os.fsencode(path)))
+
+
+def hv_layer_load_file(ctx, path):
+    out = P()
+    _check(lib().hv_layer_load_file(ctx, os.fsencode(path), ctypes.byref(out)))
+    return out.value
+
+
+def make_requests(zxyr, mode=0, layer=0):
+    """(n, 4) [z, x, y, r16] -> packed hv_tile_req records (numpy)."""
+    a = np.asarray(zxyr, dtype=np.int64).reshape(-1, 4)
+    r = np.zeros(a.shape[0], dtype=REQ_DTYPE)
+    r["z"], r["x"], r["y"], r["r16"] = a[:, 0], a[:, 1], a[:, 2], a[:, 3]
+    r["mode"] = mode
+    r["layer"] = layer
+    return r
+
+
+def make_style(line=(0, 0, 0), fill=(0, 0, 0)):
+    s = hv_style()
+    for k in range(3):
+        s.line_rgba[k] = line[k]
+        s.fill_rgba[k] = fill[k]
+    return s
+
+
+def hv_render_tiles(layer, reqs, n, mode, index_kind, style, out, out_bytes, stream=None):
+    """reqs / out: numpy arrays, torch tensors or addresses (host or device)."""
+    _check(lib().hv_render_tiles(layer, ptr(reqs), n, mode, index_kind,
+                                 ctypes.byref(style) if style is not None else None, ptr(out),
+                                 out_bytes, stream_handle(stream)))
+
+
+def hv_render_tiles_counted(layer, reqs, n, mode, index_kind, style, out, out_bytes, log, log_cap,
+                            log_count, stream=None):
+    _check(lib().hv_render_tiles_counted(layer, ptr(reqs), n, mode, index_kind,
+                                         ctypes.byref(style) if style is not None else None, ptr(out),
+                                         out_bytes, ptr(log), log_cap, ptr(log_count),
+                                         stream_handle(stream)))
+
+
+def hv_layer_take_status(layer, stream=None):
+    out = U32()
+    _check(lib().hv_layer_take_status(layer, stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def hv_render_launches(layer, index_kind=HV_INDEX_RTREE):
+    out = U32()
+    _check(lib().hv_render_launches(layer, index_kind, ctypes.byref(out)))
+    return out.value
+
+
+def hv_server_start(ctx, layers, opts):
+    arr = (P * len(layers))(*layers)
+    out = P()
+    _check(lib().hv_server_start(ctx, arr, len(layers), ctypes.byref(opts), ctypes.byref(out)))
+    return out.value
+
+
+def hv_server_submit(srv, req, tag):
+    """Returns the raw status (HV_OK or HV_EBUSY); raises on other errors."""
+    rc = lib().hv_server_submit(srv, ptr(req), tag)
+    if rc not in (HV_OK, HV_EBUSY):
+        _check(rc)
+    return rc
+
+
+def hv_server_poll(srv, buf):
+    n = U32()
+    _check(lib().hv_server_poll(srv, buf, len(buf), ctypes.byref(n)))
+    return n.value
+
+
+def hv_server_stop(srv):
+    _check(lib().hv_server_stop(srv))
+
+
+# ---- convenience: render host arrays into a numpy result --------------------
+
+def render(layer, zxyr, mode, style=None, index_kind=HV_INDEX_RTREE):
+    """Render tiles with host requests into a host array (n, tile_bytes)."""
+    reqs = make_requests(zxyr)
+    n = reqs.shape[0]
+    tb = hv_tile_bytes(mode)
+    out = np.zeros((max(n, 1), tb), dtype=np.uint8)
+    hv_render_tiles(layer, reqs, n, mode, index_kind, style, out, n * tb)
+    return out[:n]

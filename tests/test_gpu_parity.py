@@ -1,0 +1,268 @@
+"""GPU parity: CUDA tiles through the C ABI vs the CPU oracle, byte for byte.
+
+Results are exact integer decisions, so the tolerance is zero everywhere
+(HiVision Algorithm 1 and Algorithm 2 on the integer grid).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from geom import (at, lines_to_arrays, polys_to_arrays, random_cluster_points,
+                  random_star_polygons, random_walk_lines, ring_px)
+from workloads import gen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2005_12489_gb300 import hv  # noqa: E402
+
+STYLE_T = (230, 40, 20, 0, 30, 90, 200, 0)
+MODES = [hv.HV_MODE_MASK, hv.HV_MODE_COVERAGE, hv.HV_MODE_RGBA]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = hv.hv_create(0)
+    yield c
+    hv.hv_destroy(c)
+
+
+def style():
+    return hv.make_style(STYLE_T[:3], STYLE_T[4:7])
+
+
+def render_dev(layer, reqs, mode, index=hv.HV_INDEX_RTREE):
+    """Device requests and device output (the benchmark's launch form)."""
+    n = len(reqs)
+    d_req = torch.from_numpy(hv.make_requests(reqs).view(np.uint8).copy()).cuda()
+    out = torch.full((max(n, 1), hv.hv_tile_bytes(mode)), 0xAB, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    hv.hv_render_tiles(layer, d_req, n, mode, index, style(), out, out.numel(), s)
+    s.synchronize()
+    return out[:n].cpu().numpy()
+
+
+def points_layer(ctx, pts):
+    L = hv.hv_layer_load_points(ctx, pts)
+    hv.hv_layer_build_index(L)
+    return L
+
+
+def check_points(ctx, pts, reqs, modes=MODES):
+    L = points_layer(ctx, pts)
+    try:
+        for mode in modes:
+            got = render_dev(L, reqs, mode)
+            ref = oracle.render_points(pts, reqs, mode, STYLE_T)
+            bad = np.nonzero((got != ref).any(axis=1))[0]
+            assert bad.size == 0, "mode %d: %d tiles differ, first %s" % (mode, bad.size, reqs[bad[0]])
+    finally:
+        hv.hv_layer_free(L)
+
+
+def check_lines(ctx, xy, off, reqs, modes=MODES):
+    L = hv.hv_layer_load_linestrings(ctx, xy, off)
+    hv.hv_layer_build_index(L)
+    try:
+        for mode in modes:
+            got = render_dev(L, reqs, mode)
+            ref = oracle.render_lines(xy, off, reqs, mode, STYLE_T)
+            bad = np.nonzero((got != ref).any(axis=1))[0]
+            assert bad.size == 0, "mode %d: %d tiles differ, first %s" % (mode, bad.size, reqs[bad[0]])
+    finally:
+        hv.hv_layer_free(L)
+
+
+def check_polygons(ctx, xy, ro, po, reqs, modes=MODES):
+    L = hv.hv_layer_load_polygons(ctx, xy, ro, po)
+    hv.hv_layer_build_index(L)
+    try:
+        for mode in modes:
+            got = render_dev(L, reqs, mode)
+            ref = oracle.render_polygons(xy, ro, po, reqs, mode, STYLE_T)
+            bad = np.nonzero((got != ref).any(axis=1))[0]
+            assert bad.size == 0, "mode %d: %d tiles differ, first %s" % (mode, bad.size, reqs[bad[0]])
+    finally:
+        hv.hv_layer_free(L)
+
+
+# ---- the small workload: 100,000 uniform points, all 341 tiles of z 0-4 ----
+
+def test_uniform_points_all_tiles_zoom_0_to_4(ctx):
+    pts, reqs = gen.config1()
+    check_points(ctx, pts, reqs)
+
+
+# ---- random layers across zooms, radii and modes ---------------------------
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_clustered_points(ctx, seed):
+    pts = gen.gmm_points(200_000, seed=seed, k=16)
+    r16 = [1, 7, 16, 32, 100, 1024]
+    reqs = gen.density_tiles(pts, 120, 0, 19, r16, seed=seed + 50)
+    check_points(ctx, pts, reqs)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_lines(ctx, seed):
+    xy, off = gen.walk_lines(20_000, 150_000, seed=seed, n_cities=40)
+    mids = gen.segment_midpoints(xy, off, 5000, seed=seed)
+    reqs = gen.density_tiles(mids, 100, 2, 18, [1, 8, 16, 24, 64, 400], seed=seed + 60)
+    check_lines(ctx, xy, off, reqs)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_polygons(ctx, seed):
+    xy, ro, po = gen.star_polygons(20_000, seed=seed, k=16, rho_median=1e-3)
+    cen = gen.polygon_centres(xy, ro, po)
+    reqs = gen.density_tiles(cen, 80, 2, 16, [1, 8, 20, 90], seed=seed + 70)
+    check_polygons(ctx, xy, ro, po, reqs)
+
+
+def test_polygons_with_holes_and_lattice_vertices(ctx):
+    rng = np.random.default_rng(5)
+    z, tx, ty = 13, 3000, 5000
+    polys = random_star_polygons(rng, 60, z, tx, ty, 30, 128, 128, 60, holes=True, snap=True)
+    polys += [[ring_px(z, tx, ty, 100, 100, [(0, -7), (7, 0), (0, 7), (-7, 0)])],
+              [ring_px(z, tx, ty, 40, 40, [(0, 0), (8, 0), (8, 8), (0, 8), (-4, 4)])]]
+    xy, ro, po = polys_to_arrays(polys)
+    reqs = np.array([[z, tx, ty, r] for r in (1, 8, 16, 40)] +
+                    [[z + 1, 2 * tx + 1, 2 * ty, 8], [z - 1, tx // 2, ty // 2, 8]], dtype=np.uint32)
+    check_polygons(ctx, xy, ro, po, reqs)
+
+
+def test_lines_with_degenerate_segments(ctx):
+    rng = np.random.default_rng(8)
+    z, tx, ty = 12, 1000, 2000
+    lines = random_walk_lines(rng, 40, 8, z, tx, ty, 4, 128, 128, 50)
+    lines += [[at(z, tx, ty, 20, 20)] * 3,                 # zero-length segments
+              [at(z, tx, ty, 5, 5)],                        # a single vertex draws nothing
+              [at(z, tx, ty, 10, 200), at(z, tx, ty, 250, 200)]]  # level segment
+    xy, off = lines_to_arrays(lines)
+    reqs = np.array([[z, tx, ty, r] for r in (1, 8, 16, 33, 200)], dtype=np.uint32)
+    check_lines(ctx, xy, off, reqs)
+
+
+# ---- edge cases -----------------------------------------------------------
+
+def test_dense_duplicates_and_tile_borders(ctx):
+    z, tx, ty = 10, 300, 517
+    rng = np.random.default_rng(4)
+    p = random_cluster_points(rng, 5000, z, tx, ty, 0.3, 255, 0)   # a tight cluster on a corner
+    p = np.concatenate([p, p[:1000], np.array([at(z, tx, ty, 0, 0, -0.5, -0.5)], np.int32)])
+    reqs = np.array([[z, tx + a, ty + b, r] for a in (-1, 0, 1) for b in (-1, 0, 1) for r in (3, 40)],
+                    dtype=np.uint32)
+    check_points(ctx, p, reqs)
+
+
+def test_grid_extremes(ctx):
+    half = 1 << 30
+    p = np.array([[-half, -half], [half - 1, half - 1], [-half, half - 1], [half - 1, -half], [0, 0],
+                  [-1, -1]], dtype=np.int32)
+    reqs = [[0, 0, 0, 1024], [0, 0, 0, 1], [1, 0, 0, 77], [1, 1, 1, 77], [19, 0, 0, 1024],
+            [19, (1 << 19) - 1, (1 << 19) - 1, 1024], [19, 1 << 18, 1 << 18, 16],
+            [19, (1 << 18) - 1, (1 << 18) - 1, 16], [5, 15, 16, 300]]
+    check_points(ctx, p, np.array(reqs, dtype=np.uint32))
+
+
+def test_empty_and_single_object_layers(ctx):
+    reqs = np.array([[0, 0, 0, 16], [7, 64, 64, 40]], dtype=np.uint32)
+    check_points(ctx, np.zeros((0, 2), np.int32), reqs)
+    check_points(ctx, np.array([[5, -7]], np.int32), reqs)
+    xy, off = lines_to_arrays([[(0, 0)]])
+    check_lines(ctx, xy, off, reqs)
+    xy, ro, po = polys_to_arrays([])
+    check_polygons(ctx, np.zeros((0, 2), np.int32), np.array([0], np.uint64), np.array([0], np.uint64), reqs)
+
+
+def test_many_tiles_ragged_count(ctx):
+    pts = gen.gmm_points(300_000, seed=9, k=32)
+    reqs = gen.density_tiles(pts, 1237, 4, 15, 24, seed=19)
+    check_points(ctx, pts, reqs, modes=[hv.HV_MODE_COVERAGE])
+
+
+def test_host_and_device_buffers_agree(ctx):
+    pts = gen.gmm_points(50_000, seed=21, k=8)
+    reqs = gen.density_tiles(pts, 40, 5, 12, 20, seed=22)
+    L = points_layer(ctx, pts)
+    try:
+        a = hv.render(L, reqs, hv.HV_MODE_RGBA, style())          # host requests, host output
+        b = render_dev(L, reqs, hv.HV_MODE_RGBA)
+        assert np.array_equal(a, b)
+        # host requests, device output
+        out = torch.zeros((len(reqs), hv.hv_tile_bytes(hv.HV_MODE_RGBA)), dtype=torch.uint8, device="cuda")
+        hv.hv_render_tiles(L, hv.make_requests(reqs), len(reqs), hv.HV_MODE_RGBA, hv.HV_INDEX_RTREE,
+                           style(), out, out.numel(), None)
+        assert np.array_equal(out.cpu().numpy(), a)
+    finally:
+        hv.hv_layer_free(L)
+
+
+def test_errors(ctx):
+    pts = gen.uniform_points(1000, seed=1)
+    L = points_layer(ctx, pts)
+    try:
+        out = np.zeros((2, 8192), dtype=np.uint8)
+        for bad in ([20, 0, 0, 16], [3, 8, 0, 16], [3, 0, 0, 0], [3, 0, 0, 1025]):
+            with pytest.raises(hv.HVError) as e:
+                hv.hv_render_tiles(L, hv.make_requests([bad]), 1, hv.HV_MODE_MASK, hv.HV_INDEX_RTREE,
+                                   None, out, out.nbytes)
+            assert e.value.status == hv.HV_ERANGE
+        with pytest.raises(hv.HVError) as e:
+            hv.hv_render_tiles(L, hv.make_requests([[1, 0, 0, 16]] * 2), 2, hv.HV_MODE_MASK,
+                               hv.HV_INDEX_RTREE, None, out, 8192)
+        assert e.value.status == hv.HV_EINVAL
+        with pytest.raises(hv.HVError) as e:
+            hv.hv_render_tiles(L, hv.make_requests([[1, 0, 0, 16]]), 1, 7, hv.HV_INDEX_RTREE, None, out,
+                               out.nbytes)
+        assert e.value.status == hv.HV_EINVAL
+        # invalid device requests: zero tiles and a sticky status bit
+        reqs = [[2, 1, 1, 16], [2, 9, 0, 16], [30, 0, 0, 16]]
+        got = render_dev(L, np.array(reqs, dtype=np.int64), hv.HV_MODE_MASK)
+        assert not got[1].any() and not got[2].any() and got[0].any()
+        assert hv.hv_layer_take_status(L) == 1
+        assert hv.hv_layer_take_status(L) == 0
+    finally:
+        hv.hv_layer_free(L)
+    with pytest.raises(hv.HVError) as e:
+        hv.hv_layer_load_points(ctx, np.array([[1 << 30, 0]], dtype=np.int64).astype(np.int32))
+    assert e.value.status == hv.HV_ERANGE
+    with pytest.raises(hv.HVError) as e:
+        hv.hv_layer_load_linestrings(ctx, np.zeros((3, 2), np.int32), np.array([0, 2, 1, 3], np.uint64))
+    assert e.value.status == hv.HV_EINVAL
+
+
+def test_memory_budget(ctx):
+    small = hv.hv_create(0, 1 << 20)
+    try:
+        with pytest.raises(hv.HVError) as e:
+            hv.hv_layer_load_points(small, gen.uniform_points(200_000, seed=3))
+        assert e.value.status == hv.HV_ENOMEM
+        assert hv.hv_ctx_device_bytes(small) == 0
+    finally:
+        hv.hv_destroy(small)
+
+
+# ---- full-size workload in the benchmark's launch form, sampled ---------
+
+@pytest.mark.slow
+def test_clustered_100m_points_sampled_tiles(ctx):
+    """100M clustered points, 10,000 density-weighted tiles (zoom 8-14,
+    radius 2 px, RGBA) rendered in one call; 48 tiles spread over the batch
+    (densest and emptiest included) checked against the oracle."""
+    pts, reqs = gen.config2()
+    L = points_layer(ctx, pts)
+    try:
+        got = render_dev(L, reqs, hv.HV_MODE_RGBA)
+        alpha = got.reshape(len(reqs), -1, 4)[:, :, 3]
+        lit = (alpha > 0).sum(1)
+        pick = set(np.argsort(lit)[-8:].tolist()) | set(np.argsort(lit)[:4].tolist())
+        pick |= set(np.random.default_rng(0).choice(len(reqs), 36, replace=False).tolist())
+        pick = np.array(sorted(pick))
+        ref = oracle.render_points(pts, reqs[pick], hv.HV_MODE_RGBA, STYLE_T)
+        bad = [int(pick[k]) for k in range(len(pick)) if not np.array_equal(got[pick[k]], ref[k])]
+        assert not bad, "tiles differ: %s" % bad
+    finally:
+        hv.hv_layer_free(L)
