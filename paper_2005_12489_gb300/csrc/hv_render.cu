@@ -89,43 +89,51 @@ struct Smem {
     const int32_t* lvl_base[kMaxLevels + 1];
     uint32_t stk_node[kWarps][kMaxLevels + 1];
     uint32_t stk_mask[kWarps][kMaxLevels + 1];
+    uint32_t lanemask[kWarps][kMaxLevels + 1][32];
     int f_count, f_level, f_buf, next_count, next_block;
 };
 
-// Per-lane state of one pixel block.
+// Per-lane state of one 8 x 4 pixel block (lane l = pixel (l & 7, l >> 3)).
 struct Lane {
-    int32_t cx, cy, off;       // pixel centre, super-sample offset (0 in MASK mode)
-    int32_t R;
+    int32_t cx, cy;        // pixel centre
+    int32_t off;           // super-sample offset (0 in MASK mode and for fill)
+    int32_t ext;           // reach of a lane's samples: R + off (Chebyshev)
     int64_t R2;
-    uint32_t und;              // undecided samples (bit k: sample k)
-    int32_t qx0, qy0, qx1, qy1;  // query box: undecided samples +- R (warp-uniform)
-    bool done;                 // warp-uniform: every sample decided
+    uint32_t und;          // this lane's undecided samples (bit k: sample k)
+    uint32_t U;            // warp-uniform: lanes with an undecided sample
+    int64_t bx0, by0;      // warp-uniform: centre of the block's first pixel
+    int L;                 // warp-uniform: log2 of the pixel size
 };
 
 __device__ __forceinline__ int32_t sample_x(const Lane& s, int k) { return s.cx + ((k & 1) ? s.off : -s.off); }
 __device__ __forceinline__ int32_t sample_y(const Lane& s, int k) { return s.cy + ((k & 2) ? s.off : -s.off); }
 
-// Recompute the warp's query box from its undecided samples.
-__device__ __forceinline__ void refresh(Lane& s, int32_t expand) {
-    int32_t x0 = kEmptyLo, y0 = kEmptyLo, x1 = kEmptyHi, y1 = kEmptyHi;
-    if (s.und) {
-        x0 = (s.und & 5u) ? s.cx - s.off : s.cx + s.off;
-        x1 = (s.und & 10u) ? s.cx + s.off : s.cx - s.off;
-        y0 = (s.und & 3u) ? s.cy - s.off : s.cy + s.off;
-        y1 = (s.und & 12u) ? s.cy + s.off : s.cy - s.off;
-    }
-    s.done = __ballot_sync(kFull, s.und != 0) == 0;
-    x0 = __reduce_min_sync(kFull, x0);
-    y0 = __reduce_min_sync(kFull, y0);
-    x1 = __reduce_max_sync(kFull, x1);
-    y1 = __reduce_max_sync(kFull, y1);
-    s.qx0 = x0 - expand;
-    s.qy0 = y0 - expand;
-    s.qx1 = x1 + expand;
-    s.qy1 = y1 + expand;
+// Lanes of the block that have a sample within Chebyshev distance `ext` of
+// the box [x0, x1] x [y0, y1]: a pixel column c qualifies when its centre
+// lies in [x0 - ext, x1 + ext], i.e. ceil((x0-ext-bx0)/ps) <= c <=
+// floor((x1+ext-bx0)/ps), and likewise for rows.  A necessary condition for
+// any object inside the box to cover any of that lane's samples.
+__device__ __forceinline__ uint32_t rect_lanes(const Lane& s, int32_t x0, int32_t y0, int32_t x1,
+                                               int32_t y1) {
+    int64_t ax = (int64_t)x0 - s.ext - s.bx0, bx = (int64_t)x1 + s.ext - s.bx0;
+    int64_t ay = (int64_t)y0 - s.ext - s.by0, by = (int64_t)y1 + s.ext - s.by0;
+    int64_t c0 = -((-ax) >> s.L), c1 = bx >> s.L;
+    int64_t r0 = -((-ay) >> s.L), r1 = by >> s.L;
+    c0 = c0 < 0 ? 0 : c0;
+    r0 = r0 < 0 ? 0 : r0;
+    c1 = c1 > 7 ? 7 : c1;
+    r1 = r1 > 3 ? 3 : r1;
+    if (c0 > c1 || r0 > r1) return 0u;
+    uint32_t col = (0xFFu << (int)c0) & (0xFFu >> (7 - (int)c1));
+    uint32_t rows = (0x01010101u << (8 * (int)r0)) & (0x01010101u >> (8 * (3 - (int)r1)));
+    return col * rows;
 }
 
 // ---- leaf visitors -----------------------------------------------------------
+// Each lane loads one object of the leaf; objects that can reach an
+// undecided lane are broadcast one at a time and every lane in their reach
+// evaluates the exact predicate on its undecided samples.  After each object
+// the undecided set is re-balloted and the remaining objects re-filtered.
 
 struct PointLeaf {
     static constexpr bool kFill = false;
@@ -134,21 +142,27 @@ struct PointLeaf {
         log_read(p, kLogLeaf, leaf, lane);
         int2 o = make_int2(kEmptyHi, kEmptyHi);
         if (i < p.tree.n_obj) o = __ldg((const int2*)p.obj + i);
-        bool hit = o.x >= s.qx0 && o.x <= s.qx1 && o.y >= s.qy0 && o.y <= s.qy1;
-        uint32_t m = __ballot_sync(kFull, hit);
-        if (!m) return;
+        uint32_t pm = rect_lanes(s, o.x, o.y, o.x, o.y);
+        uint32_t m = __ballot_sync(kFull, (pm & s.U) != 0);
         while (m) {
             int k = __ffs(m) - 1;
             m &= m - 1;
             int32_t ox = __shfl_sync(kFull, o.x, k), oy = __shfl_sync(kFull, o.y, k);
-            uint32_t u = s.und;
-            while (u) {
-                int b = __ffs(u) - 1;
-                u &= u - 1;
-                if (point_within(ox, oy, sample_x(s, b), sample_y(s, b), s.R2)) s.und &= ~(1u << b);
+            uint32_t pmk = __shfl_sync(kFull, pm, k);
+            if ((pmk >> lane) & 1u) {
+                uint32_t u = s.und;
+                while (u) {
+                    int b = __ffs(u) - 1;
+                    u &= u - 1;
+                    if (point_within(ox, oy, sample_x(s, b), sample_y(s, b), s.R2)) s.und &= ~(1u << b);
+                }
+            }
+            uint32_t U2 = __ballot_sync(kFull, s.und != 0);
+            if (U2 != s.U) {
+                s.U = U2;
+                m &= __ballot_sync(kFull, (pm & U2) != 0);
             }
         }
-        refresh(s, s.R);
     }
 };
 
@@ -159,24 +173,29 @@ struct SegLeaf {
         log_read(p, kLogLeaf, leaf, lane);
         int4 o = make_int4(kEmptyHi, kEmptyHi, kEmptyHi, kEmptyHi);
         if (i < p.tree.n_obj) o = __ldg((const int4*)p.obj + i);
-        bool hit = min(o.x, o.z) <= s.qx1 && max(o.x, o.z) >= s.qx0 && min(o.y, o.w) <= s.qy1 &&
-                   max(o.y, o.w) >= s.qy0;
-        uint32_t m = __ballot_sync(kFull, hit);
-        if (!m) return;
+        uint32_t pm = rect_lanes(s, min(o.x, o.z), min(o.y, o.w), max(o.x, o.z), max(o.y, o.w));
+        uint32_t m = __ballot_sync(kFull, (pm & s.U) != 0);
         while (m) {
             int k = __ffs(m) - 1;
             m &= m - 1;
             int32_t ax = __shfl_sync(kFull, o.x, k), ay = __shfl_sync(kFull, o.y, k);
             int32_t bx = __shfl_sync(kFull, o.z, k), by = __shfl_sync(kFull, o.w, k);
-            uint32_t u = s.und;
-            while (u) {
-                int b = __ffs(u) - 1;
-                u &= u - 1;
-                if (segment_within(ax, ay, bx, by, sample_x(s, b), sample_y(s, b), s.R2))
-                    s.und &= ~(1u << b);
+            uint32_t pmk = __shfl_sync(kFull, pm, k);
+            if ((pmk >> lane) & 1u) {
+                uint32_t u = s.und;
+                while (u) {
+                    int b = __ffs(u) - 1;
+                    u &= u - 1;
+                    if (segment_within(ax, ay, bx, by, sample_x(s, b), sample_y(s, b), s.R2))
+                        s.und &= ~(1u << b);
+                }
+            }
+            uint32_t U2 = __ballot_sync(kFull, s.und != 0);
+            if (U2 != s.U) {
+                s.U = U2;
+                m &= __ballot_sync(kFull, (pm & U2) != 0);
             }
         }
-        refresh(s, s.R);
     }
 };
 
@@ -193,8 +212,8 @@ struct FillLeaf {
             b = __ldg(p.mbr_obj + i);
             id = __ldg(p.mbr_ids + i);
         }
-        uint32_t m = __ballot_sync(kFull, box_hit(b, s.qx0, s.qy0, s.qx1, s.qy1));
-        if (!m) return;
+        uint32_t pm = rect_lanes(s, b.x, b.y, b.z, b.w);
+        uint32_t m = __ballot_sync(kFull, (pm & s.U) != 0);
         while (m) {
             int k = __ffs(m) - 1;
             m &= m - 1;
@@ -217,35 +236,46 @@ struct FillLeaf {
                 }
             }
             if (active && parity) s.und = 0;
+            uint32_t U2 = __ballot_sync(kFull, s.und != 0);
+            if (U2 != s.U) {
+                s.U = U2;
+                m &= __ballot_sync(kFull, (pm & U2) != 0);
+            }
         }
-        refresh(s, 0);
     }
 };
 
-// Ballot of the children of node `node` at level `lvl` whose boxes meet the
-// warp's query box.
+// Child boxes of one inner node: lane c computes the lanes child c can
+// reach, keeps it in `lm`, and the ballot selects the children to visit.
 __device__ __forceinline__ uint32_t child_hits(const Params& p, bool fill, const int32_t* base,
-                                               const Lane& s, int lane) {
+                                               const Lane& s, int lane, uint32_t* lm) {
     if (p.log != nullptr)
         log_read(p, fill ? kLogPolyNode : kLogNode,
                  (uint64_t)(base - (fill ? p.mtree.nodes : p.tree.nodes)) >> 7, lane);
-    int4 b = make_int4(__ldg(base + lane), __ldg(base + 32 + lane), __ldg(base + 64 + lane),
-                       __ldg(base + 96 + lane));
-    return __ballot_sync(kFull, box_hit(b, s.qx0, s.qy0, s.qx1, s.qy1));
+    int32_t x0 = __ldg(base + lane), y0 = __ldg(base + 32 + lane);
+    int32_t x1 = __ldg(base + 64 + lane), y1 = __ldg(base + 96 + lane);
+    uint32_t cm = rect_lanes(s, x0, y0, x1, y1);
+    lm[lane] = cm;
+    return __ballot_sync(kFull, (cm & s.U) != 0);
 }
 
-// Depth-first descent from node `node` at level `level` (>= 1).
+// Depth-first descent from node `node` at level `level` (>= 1).  The stack
+// keeps, per level, the node whose children are being visited, the children
+// still to visit, and each child's lane reach (re-tested against the
+// shrinking undecided set before every visit).
 template <class V>
 __device__ void descend(const Params& p, Smem& sm, int level, uint32_t node, Lane& s, int lane, int warp) {
     uint32_t* stk_node = sm.stk_node[warp];
     uint32_t* stk_mask = sm.stk_mask[warp];
     int lvl = level;
-    uint32_t m0 = child_hits(p, V::kFill, sm.lvl_base[lvl] + (uint64_t)node * 128, s, lane);
+    uint32_t m0 = child_hits(p, V::kFill, sm.lvl_base[lvl] + (uint64_t)node * 128, s, lane,
+                             sm.lanemask[warp][lvl]);
     stk_node[lvl] = node;
     stk_mask[lvl] = m0;
     __syncwarp();
     while (true) {
         uint32_t m = stk_mask[lvl];
+        m = __ballot_sync(kFull, ((m >> lane) & 1u) && (sm.lanemask[warp][lvl][lane] & s.U));
         if (m == 0) {
             if (lvl == level) break;
             lvl++;
@@ -258,10 +288,11 @@ __device__ void descend(const Params& p, Smem& sm, int level, uint32_t node, Lan
         __syncwarp();
         if (lvl == 1) {
             V::visit(p, child, s, lane);
-            if (s.done) return;
+            if (s.U == 0) return;
         } else {
             lvl--;
-            uint32_t hm = child_hits(p, V::kFill, sm.lvl_base[lvl] + (uint64_t)child * 128, s, lane);
+            uint32_t hm = child_hits(p, V::kFill, sm.lvl_base[lvl] + (uint64_t)child * 128, s, lane,
+                                     sm.lanemask[warp][lvl]);
             stk_node[lvl] = child;
             stk_mask[lvl] = hm;
             __syncwarp();
@@ -331,7 +362,8 @@ template <class V>
 __device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, int strip, int z,
                             int32_t R, bool mask_mode, int tid) {
     int lane = tid & 31, warp = tid >> 5;
-    int32_t ps = 1 << (23 - z);
+    const int L = 23 - z;
+    const int32_t ps = 1 << L;
     const int f_count = sm.f_count, f_level = sm.f_level, fb = sm.f_buf;
     while (true) {
         int blk = 0;
@@ -343,9 +375,11 @@ __device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, i
         int jl = by * kBH + (lane >> 3);
         int j = strip * kStripRows + jl;
         Lane s;
+        s.L = L;
         s.cx = X0 + i * ps + (ps >> 1);
         s.cy = Y0 + j * ps + (ps >> 1);
-        s.R = R;
+        s.bx0 = (int64_t)X0 + (int64_t)(bx * kBW) * ps + (ps >> 1);
+        s.by0 = (int64_t)Y0 + (int64_t)(strip * kStripRows + by * kBH) * ps + (ps >> 1);
         s.R2 = (int64_t)R * R;
         if (V::kFill) {
             s.off = 0;
@@ -354,13 +388,18 @@ __device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, i
             s.off = mask_mode ? 0 : (ps >> 2);
             s.und = mask_mode ? 1u : 15u;
         }
+        s.ext = (V::kFill ? 0 : R) + s.off;
+        s.U = kFull;
         uint32_t und0 = s.und;
-        refresh(s, V::kFill ? 0 : R);
-        for (int c0 = 0; c0 < f_count && !s.done; c0 += 32) {
+        for (int c0 = 0; c0 < f_count && s.U; c0 += 32) {
             int e = c0 + lane;
-            bool hit = e < f_count && box_hit(sm.fbox[fb][e], s.qx0, s.qy0, s.qx1, s.qy1);
-            uint32_t m = __ballot_sync(kFull, hit);
-            while (m && !s.done) {
+            uint32_t cm = 0;
+            if (e < f_count) {
+                int4 fbx = sm.fbox[fb][e];
+                cm = rect_lanes(s, fbx.x, fbx.y, fbx.z, fbx.w);
+            }
+            uint32_t m = __ballot_sync(kFull, (cm & s.U) != 0);
+            while (m) {
                 int k = __ffs(m) - 1;
                 m &= m - 1;
                 uint32_t id = sm.fid[fb][c0 + k];
@@ -369,12 +408,8 @@ __device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, i
                 } else {
                     descend<V>(p, sm, f_level, id, s, lane, warp);
                 }
-                if (m) {
-                    // drop frontier entries the shrunken box no longer meets
-                    bool still = e < f_count && ((m >> lane) & 1u) &&
-                                 box_hit(sm.fbox[fb][e], s.qx0, s.qy0, s.qx1, s.qy1);
-                    m = __ballot_sync(kFull, still);
-                }
+                // drop frontier entries that no longer reach an undecided lane
+                m &= __ballot_sync(kFull, (cm & s.U) != 0);
             }
         }
         uint32_t covered = und0 & ~s.und;
