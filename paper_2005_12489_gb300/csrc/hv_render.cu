@@ -129,6 +129,39 @@ __device__ __forceinline__ uint32_t rect_lanes(const Lane& s, int32_t x0, int32_
     return col * rows;
 }
 
+// Does the box [x0, x1] x [y0, y1] come within Euclidean distance R of the
+// sample square [c - off, c + off]^2 of one of the lanes in `cand`?  Walks
+// the candidate lanes and stops at the first that qualifies; it removes the
+// boxes that sit in the corners of the Chebyshev reach but outside the disc.
+__device__ __forceinline__ bool round_reach(const Lane& s, int32_t x0, int32_t y0, int32_t x1,
+                                            int32_t y1, uint32_t cand) {
+    const int64_t ps = (int64_t)1 << s.L;
+    while (cand) {
+        int l = __ffs(cand) - 1;
+        cand &= cand - 1;
+        int64_t pcx = s.bx0 + (int64_t)(l & 7) * ps;
+        int64_t pcy = s.by0 + (int64_t)(l >> 3) * ps;
+        int64_t dx = (int64_t)x0 - (pcx + s.off);
+        int64_t ex = (pcx - s.off) - (int64_t)x1;
+        dx = dx > ex ? dx : ex;
+        dx = dx > 0 ? dx : 0;
+        int64_t dy = (int64_t)y0 - (pcy + s.off);
+        int64_t ey = (pcy - s.off) - (int64_t)y1;
+        dy = dy > ey ? dy : ey;
+        dy = dy > 0 ? dy : 0;
+        if (dx * dx + dy * dy <= s.R2) return true;
+    }
+    return false;
+}
+
+// Lanes `cm` can reach and one undecided lane is really within reach.
+__device__ __forceinline__ bool reaches(const Lane& s, bool fill, uint32_t cm, int32_t x0, int32_t y0,
+                                        int32_t x1, int32_t y1) {
+    uint32_t cand = cm & s.U;
+    if (!cand) return false;
+    return fill || round_reach(s, x0, y0, x1, y1, cand);
+}
+
 // ---- leaf visitors -----------------------------------------------------------
 // Each lane loads one object of the leaf; objects that can reach an
 // undecided lane are broadcast one at a time and every lane in their reach
@@ -143,7 +176,7 @@ struct PointLeaf {
         int2 o = make_int2(kEmptyHi, kEmptyHi);
         if (i < p.tree.n_obj) o = __ldg((const int2*)p.obj + i);
         uint32_t pm = rect_lanes(s, o.x, o.y, o.x, o.y);
-        uint32_t m = __ballot_sync(kFull, (pm & s.U) != 0);
+        uint32_t m = __ballot_sync(kFull, reaches(s, false, pm, o.x, o.y, o.x, o.y));
         while (m) {
             int k = __ffs(m) - 1;
             m &= m - 1;
@@ -160,7 +193,7 @@ struct PointLeaf {
             uint32_t U2 = __ballot_sync(kFull, s.und != 0);
             if (U2 != s.U) {
                 s.U = U2;
-                m &= __ballot_sync(kFull, (pm & U2) != 0);
+                m &= __ballot_sync(kFull, ((m >> lane) & 1u) && reaches(s, false, pm, o.x, o.y, o.x, o.y));
             }
         }
     }
@@ -173,8 +206,9 @@ struct SegLeaf {
         log_read(p, kLogLeaf, leaf, lane);
         int4 o = make_int4(kEmptyHi, kEmptyHi, kEmptyHi, kEmptyHi);
         if (i < p.tree.n_obj) o = __ldg((const int4*)p.obj + i);
-        uint32_t pm = rect_lanes(s, min(o.x, o.z), min(o.y, o.w), max(o.x, o.z), max(o.y, o.w));
-        uint32_t m = __ballot_sync(kFull, (pm & s.U) != 0);
+        const int32_t sx0 = min(o.x, o.z), sy0 = min(o.y, o.w), sx1 = max(o.x, o.z), sy1 = max(o.y, o.w);
+        uint32_t pm = rect_lanes(s, sx0, sy0, sx1, sy1);
+        uint32_t m = __ballot_sync(kFull, reaches(s, false, pm, sx0, sy0, sx1, sy1));
         while (m) {
             int k = __ffs(m) - 1;
             m &= m - 1;
@@ -193,7 +227,7 @@ struct SegLeaf {
             uint32_t U2 = __ballot_sync(kFull, s.und != 0);
             if (U2 != s.U) {
                 s.U = U2;
-                m &= __ballot_sync(kFull, (pm & U2) != 0);
+                m &= __ballot_sync(kFull, ((m >> lane) & 1u) && reaches(s, false, pm, sx0, sy0, sx1, sy1));
             }
         }
     }
@@ -256,7 +290,7 @@ __device__ __forceinline__ uint32_t child_hits(const Params& p, bool fill, const
     int32_t x1 = __ldg(base + 64 + lane), y1 = __ldg(base + 96 + lane);
     uint32_t cm = rect_lanes(s, x0, y0, x1, y1);
     lm[lane] = cm;
-    return __ballot_sync(kFull, (cm & s.U) != 0);
+    return __ballot_sync(kFull, reaches(s, fill, cm, x0, y0, x1, y1));
 }
 
 // Depth-first descent from node `node` at level `level` (>= 1).  The stack
@@ -394,11 +428,12 @@ __device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, i
         for (int c0 = 0; c0 < f_count && s.U; c0 += 32) {
             int e = c0 + lane;
             uint32_t cm = 0;
+            int4 fbx = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
             if (e < f_count) {
-                int4 fbx = sm.fbox[fb][e];
+                fbx = sm.fbox[fb][e];
                 cm = rect_lanes(s, fbx.x, fbx.y, fbx.z, fbx.w);
             }
-            uint32_t m = __ballot_sync(kFull, (cm & s.U) != 0);
+            uint32_t m = __ballot_sync(kFull, reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
             while (m) {
                 int k = __ffs(m) - 1;
                 m &= m - 1;
@@ -409,7 +444,7 @@ __device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, i
                     descend<V>(p, sm, f_level, id, s, lane, warp);
                 }
                 // drop frontier entries that no longer reach an undecided lane
-                m &= __ballot_sync(kFull, (cm & s.U) != 0);
+                m &= __ballot_sync(kFull, ((m >> lane) & 1u) && reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
             }
         }
         uint32_t covered = und0 & ~s.und;
@@ -425,7 +460,7 @@ __device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, i
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_render(const Params p) {
+__global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
     __shared__ Smem sm;
     const int tid = threadIdx.x;
     const uint32_t tile = blockIdx.x / kStrips;

@@ -117,7 +117,7 @@ def test_lines(ctx, seed):
 def test_polygons(ctx, seed):
     xy, ro, po = gen.star_polygons(20_000, seed=seed, k=16, rho_median=1e-3)
     cen = gen.polygon_centres(xy, ro, po)
-    reqs = gen.density_tiles(cen, 80, 2, 16, [1, 8, 20, 48], seed=seed + 70)
+    reqs = gen.density_tiles(cen, 60, 2, 12, [1, 8, 20, 48], seed=seed + 70)
     check_polygons(ctx, xy, ro, po, reqs)
 
 
