@@ -94,19 +94,36 @@ struct Smem {
 };
 
 // Per-lane state of one 8 x 4 pixel block (lane l = pixel (l & 7, l >> 3)).
+// Sample k of a lane sits at (cx -+ off, cy -+ off): bit 0 of k picks +x,
+// bit 1 picks +y.  MASK mode and the fill use one sample, the centre.
 struct Lane {
     int32_t cx, cy;        // pixel centre
     int32_t off;           // super-sample offset (0 in MASK mode and for fill)
     int32_t ext;           // reach of a lane's samples: R + off (Chebyshev)
     int64_t R2;
     uint32_t und;          // this lane's undecided samples (bit k: sample k)
+    uint32_t Uk[4];        // warp-uniform: lanes whose sample k is undecided
     uint32_t U;            // warp-uniform: lanes with an undecided sample
-    int64_t bx0, by0;      // warp-uniform: centre of the block's first pixel
+    int nk;                // samples per lane (1 or 4)
+    int32_t bx0, by0;      // warp-uniform: centre of the block's first pixel
     int L;                 // warp-uniform: log2 of the pixel size
 };
 
 __device__ __forceinline__ int32_t sample_x(const Lane& s, int k) { return s.cx + ((k & 1) ? s.off : -s.off); }
 __device__ __forceinline__ int32_t sample_y(const Lane& s, int k) { return s.cy + ((k & 2) ? s.off : -s.off); }
+
+// Fold per-sample coverage masks (bit l: lane l's sample k was covered) into
+// the warp's undecided state.
+__device__ __forceinline__ void apply_cover(Lane& s, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            int lane) {
+    s.Uk[0] &= ~c0;
+    s.Uk[1] &= ~c1;
+    s.Uk[2] &= ~c2;
+    s.Uk[3] &= ~c3;
+    s.U = s.Uk[0] | s.Uk[1] | s.Uk[2] | s.Uk[3];
+    s.und = ((s.Uk[0] >> lane) & 1u) | (((s.Uk[1] >> lane) & 1u) << 1) | (((s.Uk[2] >> lane) & 1u) << 2) |
+            (((s.Uk[3] >> lane) & 1u) << 3);
+}
 
 // Lanes of the block that have a sample within Chebyshev distance `ext` of
 // the box [x0, x1] x [y0, y1]: a pixel column c qualifies when its centre
@@ -129,32 +146,38 @@ __device__ __forceinline__ uint32_t rect_lanes(const Lane& s, int32_t x0, int32_
     return col * rows;
 }
 
-// Does the box [x0, x1] x [y0, y1] come within Euclidean distance R of the
-// sample square [c - off, c + off]^2 of one of the lanes in `cand`?  Walks
-// the candidate lanes and stops at the first that qualifies; it removes the
-// boxes that sit in the corners of the Chebyshev reach but outside the disc.
+// Distance from v to the interval [a, b] (0 inside).
+__device__ __forceinline__ int64_t gap(int32_t a, int32_t b, int32_t v) {
+    int64_t d1 = (int64_t)a - v, d2 = (int64_t)v - b;
+    int64_t d = d1 > d2 ? d1 : d2;
+    return d > 0 ? d : 0;
+}
+
+// Does the box [x0, x1] x [y0, y1] come within Euclidean distance R of an
+// undecided sample of one of the lanes in `cand`?  Exact for every sample;
+// stops at the first that qualifies.
 __device__ __forceinline__ bool round_reach(const Lane& s, int32_t x0, int32_t y0, int32_t x1,
                                             int32_t y1, uint32_t cand) {
-    const int64_t ps = (int64_t)1 << s.L;
+    const int32_t ps = 1 << s.L;
     while (cand) {
         int l = __ffs(cand) - 1;
         cand &= cand - 1;
-        int64_t pcx = s.bx0 + (int64_t)(l & 7) * ps;
-        int64_t pcy = s.by0 + (int64_t)(l >> 3) * ps;
-        int64_t dx = (int64_t)x0 - (pcx + s.off);
-        int64_t ex = (pcx - s.off) - (int64_t)x1;
-        dx = dx > ex ? dx : ex;
-        dx = dx > 0 ? dx : 0;
-        int64_t dy = (int64_t)y0 - (pcy + s.off);
-        int64_t ey = (pcy - s.off) - (int64_t)y1;
-        dy = dy > ey ? dy : ey;
-        dy = dy > 0 ? dy : 0;
-        if (dx * dx + dy * dy <= s.R2) return true;
+        int32_t pcx = s.bx0 + (l & 7) * ps, pcy = s.by0 + (l >> 3) * ps;
+        int64_t dxm = gap(x0, x1, pcx - s.off), dxp = gap(x0, x1, pcx + s.off);
+        int64_t dym = gap(y0, y1, pcy - s.off), dyp = gap(y0, y1, pcy + s.off);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (k < s.nk && ((s.Uk[k] >> l) & 1u)) {
+                int64_t dx = (k & 1) ? dxp : dxm, dy = (k & 2) ? dyp : dym;
+                if (dx * dx + dy * dy <= s.R2) return true;
+            }
+        }
     }
     return false;
 }
 
-// Lanes `cm` can reach and one undecided lane is really within reach.
+// Lanes `cm` can reach and one of their undecided samples really is within
+// reach.  For the fill (R = 0, centres) the Chebyshev test is already exact.
 __device__ __forceinline__ bool reaches(const Lane& s, bool fill, uint32_t cm, int32_t x0, int32_t y0,
                                         int32_t x1, int32_t y1) {
     uint32_t cand = cm & s.U;
@@ -163,10 +186,9 @@ __device__ __forceinline__ bool reaches(const Lane& s, bool fill, uint32_t cm, i
 }
 
 // ---- leaf visitors -----------------------------------------------------------
-// Each lane loads one object of the leaf; objects that can reach an
-// undecided lane are broadcast one at a time and every lane in their reach
-// evaluates the exact predicate on its undecided samples.  After each object
-// the undecided set is re-balloted and the remaining objects re-filtered.
+// Points and segments: each lane takes one object of the leaf and evaluates
+// the exact predicate on the undecided samples within its reach; the
+// per-sample hits are OR-reduced over the warp.
 
 struct PointLeaf {
     static constexpr bool kFill = false;
@@ -175,27 +197,24 @@ struct PointLeaf {
         log_read(p, kLogLeaf, leaf, lane);
         int2 o = make_int2(kEmptyHi, kEmptyHi);
         if (i < p.tree.n_obj) o = __ldg((const int2*)p.obj + i);
-        uint32_t pm = rect_lanes(s, o.x, o.y, o.x, o.y);
-        uint32_t m = __ballot_sync(kFull, reaches(s, false, pm, o.x, o.y, o.x, o.y));
-        while (m) {
-            int k = __ffs(m) - 1;
-            m &= m - 1;
-            int32_t ox = __shfl_sync(kFull, o.x, k), oy = __shfl_sync(kFull, o.y, k);
-            uint32_t pmk = __shfl_sync(kFull, pm, k);
-            if ((pmk >> lane) & 1u) {
-                uint32_t u = s.und;
-                while (u) {
-                    int b = __ffs(u) - 1;
-                    u &= u - 1;
-                    if (point_within(ox, oy, sample_x(s, b), sample_y(s, b), s.R2)) s.und &= ~(1u << b);
-                }
-            }
-            uint32_t U2 = __ballot_sync(kFull, s.und != 0);
-            if (U2 != s.U) {
-                s.U = U2;
-                m &= __ballot_sync(kFull, ((m >> lane) & 1u) && reaches(s, false, pm, o.x, o.y, o.x, o.y));
+        uint32_t pm = rect_lanes(s, o.x, o.y, o.x, o.y) & s.U;
+        if (!__any_sync(kFull, pm != 0)) return;
+        const int32_t ps = 1 << s.L;
+        uint32_t c[4] = {0u, 0u, 0u, 0u};
+        while (pm) {
+            int l = __ffs(pm) - 1;
+            pm &= pm - 1;
+            int32_t pcx = s.bx0 + (l & 7) * ps, pcy = s.by0 + (l >> 3) * ps;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (k < s.nk && ((s.Uk[k] >> l) & 1u) &&
+                    point_within(o.x, o.y, pcx + ((k & 1) ? s.off : -s.off), pcy + ((k & 2) ? s.off : -s.off),
+                                 s.R2))
+                    c[k] |= 1u << l;
             }
         }
+        apply_cover(s, __reduce_or_sync(kFull, c[0]), __reduce_or_sync(kFull, c[1]),
+                    __reduce_or_sync(kFull, c[2]), __reduce_or_sync(kFull, c[3]), lane);
     }
 };
 
@@ -207,29 +226,24 @@ struct SegLeaf {
         int4 o = make_int4(kEmptyHi, kEmptyHi, kEmptyHi, kEmptyHi);
         if (i < p.tree.n_obj) o = __ldg((const int4*)p.obj + i);
         const int32_t sx0 = min(o.x, o.z), sy0 = min(o.y, o.w), sx1 = max(o.x, o.z), sy1 = max(o.y, o.w);
-        uint32_t pm = rect_lanes(s, sx0, sy0, sx1, sy1);
-        uint32_t m = __ballot_sync(kFull, reaches(s, false, pm, sx0, sy0, sx1, sy1));
-        while (m) {
-            int k = __ffs(m) - 1;
-            m &= m - 1;
-            int32_t ax = __shfl_sync(kFull, o.x, k), ay = __shfl_sync(kFull, o.y, k);
-            int32_t bx = __shfl_sync(kFull, o.z, k), by = __shfl_sync(kFull, o.w, k);
-            uint32_t pmk = __shfl_sync(kFull, pm, k);
-            if ((pmk >> lane) & 1u) {
-                uint32_t u = s.und;
-                while (u) {
-                    int b = __ffs(u) - 1;
-                    u &= u - 1;
-                    if (segment_within(ax, ay, bx, by, sample_x(s, b), sample_y(s, b), s.R2))
-                        s.und &= ~(1u << b);
-                }
-            }
-            uint32_t U2 = __ballot_sync(kFull, s.und != 0);
-            if (U2 != s.U) {
-                s.U = U2;
-                m &= __ballot_sync(kFull, ((m >> lane) & 1u) && reaches(s, false, pm, sx0, sy0, sx1, sy1));
+        uint32_t pm = rect_lanes(s, sx0, sy0, sx1, sy1) & s.U;
+        if (!__any_sync(kFull, pm != 0)) return;
+        const int32_t ps = 1 << s.L;
+        uint32_t c[4] = {0u, 0u, 0u, 0u};
+        while (pm) {
+            int l = __ffs(pm) - 1;
+            pm &= pm - 1;
+            int32_t pcx = s.bx0 + (l & 7) * ps, pcy = s.by0 + (l >> 3) * ps;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (k < s.nk && ((s.Uk[k] >> l) & 1u) &&
+                    segment_within(o.x, o.y, o.z, o.w, pcx + ((k & 1) ? s.off : -s.off),
+                                   pcy + ((k & 2) ? s.off : -s.off), s.R2))
+                    c[k] |= 1u << l;
             }
         }
+        apply_cover(s, __reduce_or_sync(kFull, c[0]), __reduce_or_sync(kFull, c[1]),
+                    __reduce_or_sync(kFull, c[2]), __reduce_or_sync(kFull, c[3]), lane);
     }
 };
 
@@ -273,6 +287,7 @@ struct FillLeaf {
             uint32_t U2 = __ballot_sync(kFull, s.und != 0);
             if (U2 != s.U) {
                 s.U = U2;
+                s.Uk[0] = U2;
                 m &= __ballot_sync(kFull, (pm & U2) != 0);
             }
         }
@@ -412,18 +427,21 @@ __device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, i
         s.L = L;
         s.cx = X0 + i * ps + (ps >> 1);
         s.cy = Y0 + j * ps + (ps >> 1);
-        s.bx0 = (int64_t)X0 + (int64_t)(bx * kBW) * ps + (ps >> 1);
-        s.by0 = (int64_t)Y0 + (int64_t)(strip * kStripRows + by * kBH) * ps + (ps >> 1);
+        s.bx0 = X0 + (bx * kBW) * ps + (ps >> 1);
+        s.by0 = Y0 + (strip * kStripRows + by * kBH) * ps + (ps >> 1);
         s.R2 = (int64_t)R * R;
-        if (V::kFill) {
+        if (V::kFill || mask_mode) {
             s.off = 0;
             s.und = 1u;
+            s.nk = 1;
         } else {
-            s.off = mask_mode ? 0 : (ps >> 2);
-            s.und = mask_mode ? 1u : 15u;
+            s.off = ps >> 2;
+            s.und = 15u;
+            s.nk = 4;
         }
         s.ext = (V::kFill ? 0 : R) + s.off;
         s.U = kFull;
+        for (int k = 0; k < 4; k++) s.Uk[k] = k < s.nk ? kFull : 0u;
         uint32_t und0 = s.und;
         for (int c0 = 0; c0 < f_count && s.U; c0 += 32) {
             int e = c0 + lane;

@@ -115,10 +115,22 @@ def test_lines(ctx, seed):
 
 @pytest.mark.parametrize("seed", [1, 2])
 def test_polygons(ctx, seed):
-    xy, ro, po = gen.star_polygons(20_000, seed=seed, k=16, rho_median=1e-3)
+    xy, ro, po = gen.star_polygons(8_000, seed=seed, k=16, rho_median=6e-4)
     cen = gen.polygon_centres(xy, ro, po)
-    reqs = gen.density_tiles(cen, 60, 2, 12, [1, 8, 20, 48], seed=seed + 70)
+    reqs = gen.density_tiles(cen, 60, 2, 10, [1, 8, 20, 48], seed=seed + 70)
     check_polygons(ctx, xy, ro, po, reqs)
+
+
+def test_tiles_inside_large_polygons(ctx):
+    """Rays that leave the tile: a few huge star polygons (with holes) seen at
+    high zoom, where whole tiles lie inside or straddle their edges."""
+    rng = np.random.default_rng(17)
+    polys = random_star_polygons(rng, 6, 6, 20, 30, 60, 128, 128, 30, holes=True)
+    xy, ro, po = polys_to_arrays(polys)
+    cen = gen.polygon_centres(xy, ro, po)
+    reqs = gen.density_tiles(cen, 24, 9, 15, [1, 8, 40], seed=18)
+    reqs2 = gen.density_tiles(xy, 24, 9, 15, [8], seed=19)        # tiles on the outlines
+    check_polygons(ctx, xy, ro, po, np.concatenate([reqs, reqs2]))
 
 
 def test_polygons_with_holes_and_lattice_vertices(ctx):
