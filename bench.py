@@ -27,15 +27,19 @@ sys.path.insert(0, ROOT)
 
 from workloads import gen  # noqa: E402
 
-WORKLOAD = {
-    "workload": "clustered points 100M (64-Gaussian mixture + 5% noise, int32 grid), "
-                "10,000 density-weighted 256x256 tiles at zoom 8-14, radius 2 px, RGBA",
-    "n_points": 100_000_000,
-    "tiles_per_step": 10_000,
-    "zoom": [8, 14],
-    "r16": 32,
-    "mode": "rgba",
+WORKLOADS = {
+    2: {"workload": "clustered points 100M (64-Gaussian mixture + 5% noise, int32 grid), "
+                    "10,000 density-weighted 256x256 tiles at zoom 8-14, radius 2 px, RGBA",
+        "n_objects": 100_000_000, "tiles_per_step": 10_000, "zoom": [8, 14], "r16": 32, "mode": "rgba"},
+    3: {"workload": "random-walk linestrings 50M segments in 5M lines around 1,000 city centres "
+                    "(int32 grid), 10,000 density-weighted tiles at zoom 6-16, half-width 1 px, RGBA",
+        "n_objects": 50_000_000, "n_lines": 5_000_000, "tiles_per_step": 10_000, "zoom": [6, 16],
+        "r16": 16, "mode": "rgba"},
+    4: {"workload": "star polygons 2M (8-64 vertices, 256-Gaussian mixture centres, int32 grid), "
+                    "10,000 density-weighted tiles at zoom 4-14, fill + 1 px outline, RGBA",
+        "n_objects": 2_000_000, "tiles_per_step": 10_000, "zoom": [4, 14], "r16": 8, "mode": "rgba"},
 }
+WORKLOAD = WORKLOADS[2]
 METRIC = "tiles/sec (256² px) and p99 tile latency, learned vs R-tree index, 1 GB300"
 STYLE_T = (230, 40, 20, 0, 30, 90, 200, 0)
 L2_FLUSH_BYTES = 512 << 20
@@ -47,9 +51,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--points", type=int, default=WORKLOAD["n_points"])
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4],
+                    help="2: clustered points (the headline), 3: linestrings, 4: polygons")
+    ap.add_argument("--r16", type=int, default=None)
+    ap.add_argument("--points", type=int, default=None, help="objects (points / segments / polygons)")
     ap.add_argument("--tiles", type=int, default=WORKLOAD["tiles_per_step"])
-    ap.add_argument("--cpu-sample-tiles", type=int, default=48)
+    ap.add_argument("--cpu-sample-tiles", type=int, default=None,
+                    help="oracle sample (default 48 / 16 / 6 tiles for configs 2 / 3 / 4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--count-sample-tiles", type=int, default=200)
@@ -124,24 +132,70 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+class Layer:
+    """A workload's layer as host arrays, with loaders for the library and the oracle."""
+
+    def __init__(self, cfg, args, rank):
+        w = WORKLOADS[cfg]
+        self.cfg = cfg
+        n = args.points or w["n_objects"]
+        r16 = args.r16 or w["r16"]
+        z0, z1 = w["zoom"]
+        if cfg == 2:
+            self.kind = "points"
+            self.xy = gen.gmm_points(n, seed=2, k=64)
+            self.reqs = gen.density_tiles(self.xy, args.tiles, z0, z1, r16, seed=102 + rank)
+            self.obj_bytes = 8
+        elif cfg == 3:
+            self.kind = "lines"
+            n_lines = max(1, n // 10)
+            self.xy, self.off = gen.walk_lines(n_lines, n, seed=3)
+            mids = gen.segment_midpoints(self.xy, self.off, max_n=4 * args.tiles, seed=103)
+            self.reqs = gen.density_tiles(mids, args.tiles, z0, z1, r16, seed=203 + rank)
+            self.obj_bytes = 16
+        else:
+            self.kind = "polygons"
+            self.xy, self.ro, self.po = gen.star_polygons(n, seed=4)
+            cen = gen.polygon_centres(self.xy, self.ro, self.po)
+            self.reqs = gen.density_tiles(cen, args.tiles, z0, z1, r16, seed=104 + rank)
+            self.obj_bytes = 16
+            ro = np.asarray(self.ro, dtype=np.int64)
+            po = np.asarray(self.po, dtype=np.int64)
+            self.poly_edges = ro[po[1:]] - ro[po[:-1]]
+        self.n_objects = n
+
+    def load(self, hv, ctx):
+        if self.kind == "points":
+            return hv.hv_layer_load_points(ctx, self.xy)
+        if self.kind == "lines":
+            return hv.hv_layer_load_linestrings(ctx, self.xy, self.off)
+        return hv.hv_layer_load_polygons(ctx, self.xy, self.ro, self.po)
+
+    def oracle(self, reqs, mode=2):
+        import oracle
+        oracle.build()
+        if self.kind == "points":
+            return oracle.render_points(self.xy, reqs, mode, STYLE_T)
+        if self.kind == "lines":
+            return oracle.render_lines(self.xy, self.off, reqs, mode, STYLE_T)
+        return oracle.render_polygons(self.xy, self.ro, self.po, reqs, mode, STYLE_T)
+
+
 def workload(args, rank):
-    pts = gen.gmm_points(args.points, seed=2, k=64)
-    reqs = gen.density_tiles(pts, args.tiles, 8, 14, WORKLOAD["r16"], seed=102 + rank)
-    return pts, reqs
+    return Layer(args.config, args, rank)
 
 
-def cpu_baseline(pts, reqs, n_sample):
+def cpu_baseline(lay, n_sample):
     """The oracle (single-threaded C, data driven) on a bounded sample of the
     batch's tiles: one pass over all objects for n_sample tiles."""
-    import oracle
-    oracle.build()
+    reqs = lay.reqs
     sample = reqs[np.linspace(0, len(reqs) - 1, n_sample).astype(np.int64)]
     t0 = time.perf_counter()
-    oracle.render_points(pts, sample, oracle.MODE_RGBA, STYLE_T)
+    lay.oracle(sample)
     dt = time.perf_counter() - t0
     return {"value": n_sample / dt, "unit": "tiles/s", "cores": 1, "kind": "oracle",
-            "sample": "%d of the %d tiles (evenly spaced), all %d points, single-threaded C"
-                      % (n_sample, len(reqs), len(pts)), "seconds": dt}
+            "sample": "%d of the %d tiles (evenly spaced), all %d %s, single-threaded C"
+                      % (n_sample, len(reqs), lay.n_objects, lay.kind), "seconds": dt}
 
 
 def run_reference(args):
@@ -149,15 +203,14 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    oracle.build()
-    pts, reqs = workload(args, 0)
+    lay = workload(args, 0)
+    reqs = lay.reqs
     n_sample = 8
     times = []
     for step in range(args.warmup + args.steps):
         sample = reqs[(np.arange(n_sample) * 997 + step * 13) % len(reqs)]
         t0 = time.perf_counter()
-        oracle.render_points(pts, sample, oracle.MODE_RGBA, STYLE_T)
+        lay.oracle(sample)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
@@ -166,18 +219,20 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "impl": "reference",
-            "config": dict(WORKLOAD, sample_tiles_per_step=n_sample),
+            "config": dict(WORKLOADS[args.config], sample_tiles_per_step=n_sample),
             "cpu_baseline": {"value": value, "unit": "tiles/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d tiles per step of the %d-tile batch, all %d points"
-                                       % (n_sample, len(reqs), len(pts))},
+                             "sample": "%d tiles per step of the %d-tile batch, all %d %s"
+                                       % (n_sample, len(reqs), lay.n_objects, lay.kind)},
             "e2e": {"value": value, "unit": "tiles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def algorithmic_bytes_per_tile(hv, layer, reqs_dev_np, torch, n_sample):
+def algorithmic_bytes_per_tile(hv, layer, reqs_dev_np, torch, n_sample, lay):
     """Unique bytes the early-exit traversal must read per tile (inner nodes x
-    512 B + visited leaves x 32 points x 8 B) plus the tile's output and its
-    request, from the library's instrumented visit log on a tile sample."""
+    512 B + visited leaves x 32 objects x object size, polygon boxes and the
+    edges of the polygons whose parity was evaluated) plus the tile's output
+    and its request, from the library's instrumented visit log on a tile
+    sample; non-unique visit counts are reported beside it."""
     idx = np.linspace(0, len(reqs_dev_np) - 1, n_sample).astype(np.int64)
     sample = reqs_dev_np[idx]
     log = torch.empty(1 << 27, dtype=torch.int64, device="cuda")
@@ -190,14 +245,23 @@ def algorithmic_bytes_per_tile(hv, layer, reqs_dev_np, torch, n_sample):
     n = int(cnt.item())
     if n > log.numel():
         return None
-    keys = torch.unique(log[:n])
+    visits = log[:n]
+    vkind = (visits >> 35) & 7
+    keys = torch.unique(visits)
     kind = (keys >> 35) & 7
     nodes = int((kind == 0).sum().item())
     leaves = int((kind == 1).sum().item())
-    read = nodes * 512 + leaves * 32 * 8
-    per_tile = read / len(sample) + hv.hv_tile_bytes(hv.HV_MODE_RGBA) + 16
-    return {"per_tile": per_tile, "read_per_tile": read / len(sample), "nodes_per_tile": nodes / len(sample),
-            "leaves_per_tile": leaves / len(sample), "sample_tiles": len(sample)}
+    pnodes = int((kind == 2).sum().item())
+    pleaves = int((kind == 3).sum().item())
+    read = nodes * 512 + leaves * 32 * lay.obj_bytes + pnodes * 512 + pleaves * 32 * 20
+    if lay.kind == "polygons":
+        pid = (keys[kind == 4] & ((1 << 35) - 1)).cpu().numpy()
+        read += int(lay.poly_edges[pid].sum()) * 16 + 16 * len(pid)
+    k = len(sample)
+    per_tile = read / k + hv.hv_tile_bytes(hv.HV_MODE_RGBA) + 16
+    return {"per_tile": per_tile, "read_per_tile": read / k, "unique_nodes_per_tile": nodes / k,
+            "unique_leaves_per_tile": leaves / k, "node_visits_per_tile": int((vkind == 0).sum()) / k,
+            "leaf_visits_per_tile": int((vkind == 1).sum()) / k, "sample_tiles": k}
 
 
 def run_gb300(args):
@@ -216,9 +280,10 @@ def run_gb300(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    pts, reqs = workload(args, rank)
+    lay = workload(args, rank)
+    reqs = lay.reqs
     ctx = hv.hv_create(local)
-    layer = hv.hv_layer_load_points(ctx, pts)
+    layer = lay.load(hv, ctx)
     hv.hv_layer_build_index(layer, hv.HV_INDEX_RTREE)
     info = hv.hv_layer_info_get(layer)
     mode = hv.HV_MODE_RGBA
@@ -266,7 +331,7 @@ def run_gb300(args):
     line = None
     if rank == 0:
         peak, peak_kind = measured_peak_hbm()
-        alg = algorithmic_bytes_per_tile(hv, layer, reqs, torch, args.count_sample_tiles)
+        alg = algorithmic_bytes_per_tile(hv, layer, reqs, torch, args.count_sample_tiles, lay)
         roof = None
         if alg is not None:
             achieved = alg["per_tile"] * n / (ms / 1000.0) / 1e9
@@ -288,13 +353,14 @@ def run_gb300(args):
             e2e = {"value": n / dt, "unit": "tiles/s", "h2d_bytes_per_step": int(h_req.nbytes),
                    "d2h_bytes_per_step": int(n * tb), "ms_per_step": 1000 * dt,
                    "path": "hv_render_tiles with host requests and pinned host output"}
-        cpu = None if args.no_cpu_baseline else cpu_baseline(pts, reqs, args.cpu_sample_tiles)
+        n_cpu = args.cpu_sample_tiles or {2: 48, 3: 16, 4: 6}[args.config]
+        cpu = None if args.no_cpu_baseline else cpu_baseline(lay, n_cpu)
         line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
                 "data": "synthetic",
-                "config": dict(WORKLOAD, index="packed Hilbert R-tree", l2="flushed between steps "
-                               "(512 MiB write); layer 800 MB and output 2.6 GB exceed L2",
+                "config": dict(WORKLOADS[args.config], index="packed Hilbert R-tree",
+                               l2="flushed between steps (512 MiB write); layer and 2.6 GB output exceed L2",
                                parallelism="replicas" if world > 1 else "single GPU"),
                 "pixel_queries_per_s": value * 65536,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

@@ -278,3 +278,42 @@ def test_clustered_100m_points_sampled_tiles(ctx):
         assert not bad, "tiles differ: %s" % bad
     finally:
         hv.hv_layer_free(L)
+
+
+def _sampled_check(render_gpu, render_ref, reqs, n_even, n_dense, mode=hv.HV_MODE_RGBA):
+    got = render_gpu(reqs, mode)
+    lit = (got.reshape(len(reqs), -1, 4)[:, :, 3] > 0).sum(1) if mode == hv.HV_MODE_RGBA else got.sum(1)
+    pick = set(np.argsort(lit)[-n_dense:].tolist())
+    pick |= set(np.linspace(0, len(reqs) - 1, n_even).astype(int).tolist())
+    pick = np.array(sorted(pick))
+    ref = render_ref(reqs[pick], mode)
+    bad = [int(pick[k]) for k in range(len(pick)) if not np.array_equal(got[pick[k]], ref[k])]
+    assert not bad, "tiles differ: %s" % bad
+
+
+@pytest.mark.slow
+def test_linestrings_50m_segments_sampled_tiles(ctx):
+    """50M segments in 5M random-walk lines, 10,000 density-weighted tiles
+    (zoom 6-16, half-width 1 px, RGBA) in one call; 16 tiles checked."""
+    xy, off, reqs = gen.config3()
+    L = hv.hv_layer_load_linestrings(ctx, xy, off)
+    hv.hv_layer_build_index(L)
+    try:
+        _sampled_check(lambda r, m: render_dev(L, r, m),
+                       lambda r, m: oracle.render_lines(xy, off, r, m, STYLE_T), reqs, 12, 4)
+    finally:
+        hv.hv_layer_free(L)
+
+
+@pytest.mark.slow
+def test_polygons_2m_sampled_tiles(ctx):
+    """2M star polygons (72M edges), 10,000 density-weighted tiles (zoom 4-14,
+    fill + 1 px outline, RGBA) in one call; 8 tiles checked."""
+    xy, ro, po, reqs = gen.config4()
+    L = hv.hv_layer_load_polygons(ctx, xy, ro, po)
+    hv.hv_layer_build_index(L)
+    try:
+        _sampled_check(lambda r, m: render_dev(L, r, m),
+                       lambda r, m: oracle.render_polygons(xy, ro, po, r, m, STYLE_T), reqs, 6, 2)
+    finally:
+        hv.hv_layer_free(L)

@@ -147,7 +147,8 @@ def star_polygons(n, seed, k=256, nv_min=8, nv_max=64, rho_median=2e-4, rho_sigm
     """n simple star-shaped polygons (one ring each).
 
     Centres from a k-component mixture (as ``gmm_points``); vertex count
-    uniform in [nv_min, nv_max]; vertex angles are sorted uniform draws;
+    uniform in [nv_min, nv_max]; vertex angles are sorted uniform draws
+    (drawn as normalised partial sums of exponential spacings);
     vertex radius = rho * U(0.5, 1) with rho log-normal (median rho_median of
     the extent).  After quantisation a polygon is kept only if every pair of
     consecutive vertices turns strictly counter-clockwise about its integer
@@ -160,15 +161,24 @@ def star_polygons(n, seed, k=256, nv_min=8, nv_max=64, rho_median=2e-4, rho_sigm
     pc = _draw_mixture(rng, centres, sigma, comp)
     nv = rng.integers(nv_min, nv_max + 1, size=n)
     rho = np.exp(np.log(rho_median * GRID) + rho_sigma_ln * rng.standard_normal(n))
-    polys_xy = [None] * n
+    ring_off = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(nv, out=ring_off[1:])
+    xy = np.empty((int(ring_off[-1]), 2), dtype=np.int32)
     todo = np.arange(n)
     while todo.size:
         t_nv = nv[todo]
         tot = int(t_nv.sum())
         pid = np.repeat(np.arange(todo.size), t_nv)
-        ang = rng.uniform(0, 2 * np.pi, size=tot)
-        order = np.lexsort((ang, pid))
-        ang = ang[order]
+        # sorted uniform angles per polygon without a sort: normalised partial
+        # sums of nv + 1 exponential spacings (Renyi representation)
+        e = rng.standard_exponential(tot + todo.size)
+        c = np.cumsum(e)
+        ends = np.cumsum(t_nv + 1) - 1                # index of each polygon's last spacing
+        base = np.concatenate([[0.0], c[ends[:-1]]])  # sum before each polygon
+        total = c[ends] - base
+        keep = np.ones(tot + todo.size, dtype=bool)
+        keep[ends] = False
+        ang = 2 * np.pi * (c[keep] - np.repeat(base, t_nv)) / np.repeat(total, t_nv)
         rad = np.repeat(rho[todo], t_nv) * rng.uniform(0.5, 1.0, size=tot)
         cx = np.repeat(pc[todo, 0], t_nv).astype(np.float64)
         cy = np.repeat(pc[todo, 1], t_nv).astype(np.float64)
@@ -184,13 +194,13 @@ def star_polygons(n, seed, k=256, nv_min=8, nv_max=64, rho_median=2e-4, rho_sigm
         bad_v = (cross <= 0) | ~_in_grid(vx) | ~_in_grid(vy)
         bad = np.zeros(todo.size, dtype=bool)
         np.logical_or.at(bad, pid, bad_v)
-        for q in np.nonzero(~bad)[0]:
-            s, e = starts[q], starts[q + 1]
-            polys_xy[todo[q]] = np.stack([vx[s:e], vy[s:e]], axis=1)
+        keep_v = ~bad[pid]
+        # destination of each kept vertex: its polygon's final offset + rank in polygon
+        rank = np.arange(tot) - starts[pid]
+        dest = ring_off[todo[pid[keep_v]]].astype(np.int64) + rank[keep_v]
+        xy[dest, 0] = vx[keep_v]
+        xy[dest, 1] = vy[keep_v]
         todo = todo[bad]
-    ring_off = np.zeros(n + 1, dtype=np.uint64)
-    np.cumsum(nv, out=ring_off[1:])
-    xy = np.concatenate(polys_xy).astype(np.int32)
     poly_ring_off = np.arange(n + 1, dtype=np.uint64)
     return xy, ring_off, poly_ring_off
 
