@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--count-sample-tiles", type=int, default=200)
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--index", default="rtree", choices=["rtree", "learned"],
+                    help="index timed for the headline value (both are reported)")
     ap.add_argument("--profile-steps", action="store_true",
                     help="only warm-up + steps, no baselines (for ncu launch lists)")
     return ap.parse_args()
@@ -284,8 +287,10 @@ def run_gb300(args):
     reqs = lay.reqs
     ctx = hv.hv_create(local)
     layer = lay.load(hv, ctx)
-    hv.hv_layer_build_index(layer, hv.HV_INDEX_RTREE)
+    want_learned = (not args.no_learned) or args.index == "learned"
+    hv.hv_layer_build_index(layer, hv.HV_INDEX_RTREE | (hv.HV_INDEX_LEARNED if want_learned else 0))
     info = hv.hv_layer_info_get(layer)
+    main_index = hv.HV_INDEX_LEARNED if args.index == "learned" else hv.HV_INDEX_RTREE
     mode = hv.HV_MODE_RGBA
     tb = hv.hv_tile_bytes(mode)
     n = len(reqs)
@@ -294,10 +299,10 @@ def run_gb300(args):
     d_out = torch.empty((n, tb), dtype=torch.uint8, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    launches_per_step = hv.hv_render_launches(layer, hv.HV_INDEX_RTREE)
+    launches_per_step = hv.hv_render_launches(layer, main_index)
 
-    def step():
-        hv.hv_render_tiles(layer, d_req, n, mode, hv.HV_INDEX_RTREE, style, d_out, d_out.numel(), stream)
+    def step(index=main_index):
+        hv.hv_render_tiles(layer, d_req, n, mode, index, style, d_out, d_out.numel(), stream)
 
     for _ in range(args.warmup):
         flush.fill_(1)
@@ -318,6 +323,36 @@ def run_gb300(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
+
+    def timed_steps(index, k_steps):
+        for _ in range(2):
+            step(index)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k_steps)]
+        for k in range(k_steps):
+            flush.fill_(k & 255)
+            evs[k][0].record(stream)
+            step(index)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / k_steps
+
+    def latency(index, n_tiles=300):
+        """Per-tile latency: batch-1 calls, each timed with CUDA events."""
+        idx = np.linspace(0, n - 1, n_tiles).astype(np.int64)
+        one = torch.empty((1, tb), dtype=torch.uint8, device="cuda")
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n_tiles)]
+        req_rows = d_req.view(n, 16)
+        for k, t in enumerate(idx):
+            r = req_rows[int(t)]
+            evs[k][0].record(stream)
+            hv.hv_render_tiles(layer, r, 1, mode, index, style, one, one.numel(), stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        lat = np.array([a.elapsed_time(b) for a, b in evs])
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "tiles": n_tiles, "form": "batch-1 calls, device buffers"}
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -330,6 +365,20 @@ def run_gb300(args):
     # ---- extras measured on rank 0 only ----
     line = None
     if rank == 0:
+        lat = {"rtree": latency(hv.HV_INDEX_RTREE)}
+        learned = None
+        if want_learned:
+            info = hv.hv_layer_info_get(layer)
+            lms = timed_steps(hv.HV_INDEX_LEARNED, max(3, min(args.steps, 10)))
+            rms = ms if main_index == hv.HV_INDEX_RTREE else timed_steps(hv.HV_INDEX_RTREE, max(3, min(args.steps, 10)))
+            lat["learned"] = latency(hv.HV_INDEX_LEARNED)
+            learned = {"value": n / (lms / 1000.0), "ms_per_step": lms, "unit": "tiles/s",
+                       "rtree_value": n / (rms / 1000.0), "learned_over_rtree": rms / lms,
+                       "error_bound": info.learned_error, "error_bound_linear": info.learned_error_linear,
+                       "error_bound_mlp": info.learned_error_mlp, "mean_error": info.learned_mean_error,
+                       "pieces": info.learned_pieces, "mlp_in_use": bool(info.learned_mlp),
+                       "halo": info.learned_halo, "side_tree_objects": info.learned_outliers,
+                       "train_ms": info.train_ms}
         peak, peak_kind = measured_peak_hbm()
         alg = algorithmic_bytes_per_tile(hv, layer, reqs, torch, args.count_sample_tiles, lay)
         roof = None
@@ -344,11 +393,11 @@ def run_gb300(args):
             h_req = hv.make_requests(reqs)
             h_out = torch.empty((n, tb), dtype=torch.uint8, pin_memory=True)
             for _ in range(2):
-                hv.hv_render_tiles(layer, h_req, n, mode, hv.HV_INDEX_RTREE, style, h_out, h_out.numel(), stream)
+                hv.hv_render_tiles(layer, h_req, n, mode, main_index, style, h_out, h_out.numel(), stream)
             k_e2e = max(3, min(args.steps, 10))
             t1 = time.perf_counter()
             for _ in range(k_e2e):
-                hv.hv_render_tiles(layer, h_req, n, mode, hv.HV_INDEX_RTREE, style, h_out, h_out.numel(), stream)
+                hv.hv_render_tiles(layer, h_req, n, mode, main_index, style, h_out, h_out.numel(), stream)
             dt = (time.perf_counter() - t1) / k_e2e
             e2e = {"value": n / dt, "unit": "tiles/s", "h2d_bytes_per_step": int(h_req.nbytes),
                    "d2h_bytes_per_step": int(n * tb), "ms_per_step": 1000 * dt,
@@ -359,12 +408,14 @@ def run_gb300(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
                 "data": "synthetic",
-                "config": dict(WORKLOADS[args.config], index="packed Hilbert R-tree",
+                "config": dict(WORKLOADS[args.config],
+                               index="packed Hilbert R-tree" if args.index == "rtree" else "learned",
                                l2="flushed between steps (512 MiB write); layer and 2.6 GB output exceed L2",
                                parallelism="replicas" if world > 1 else "single GPU"),
                 "pixel_queries_per_s": value * 65536,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+                "index_timed": args.index, "learned": learned, "latency": lat,
                 "wall_s_timed_region": wall, "step_ms": step_ms,
                 "index_build_ms": info.build_ms, "tree_levels": info.tree_levels}
         print(json.dumps(line), flush=True)

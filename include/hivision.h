@@ -123,10 +123,18 @@ typedef struct hv_layer_info {
     uint32_t tree_levels;        /* inner levels of the object R-tree */
     uint64_t tree_nodes;         /* inner nodes of the object R-tree */
     uint64_t device_bytes;       /* device memory held by the layer */
-    int64_t learned_error;       /* learned index: max |predicted - true| position */
-    uint64_t learned_outliers;   /* learned index: objects kept in the side list */
+    int64_t learned_error;       /* learned index: max |predicted - true| position
+                                    (-1: not built) */
+    uint64_t learned_outliers;   /* learned index: objects kept in the side tree */
     double build_ms;             /* last index build, device time */
     double train_ms;             /* learned-index training, device time */
+    int64_t learned_error_linear;  /* error bound of the linear pieces alone */
+    int64_t learned_error_mlp;     /* error bound with the MLP residual */
+    double learned_mean_error;     /* mean |predicted - true| position */
+    uint32_t learned_pieces;       /* piecewise-linear pieces */
+    uint32_t learned_mlp;          /* 1 if the MLP residual is in use */
+    int32_t learned_halo;          /* half-extent covered through centre keys */
+    int32_t reserved;
 } hv_layer_info;
 
 /* ---- context ------------------------------------------------------------ */
@@ -171,6 +179,17 @@ int hv_layer_load_polygons(hv_ctx* ctx, const int32_t* xy, uint64_t n_vert,
 int hv_layer_build_index(hv_layer* layer, uint32_t kinds, const hv_build_opts* opts);
 
 int hv_layer_info_get(hv_layer* layer, hv_layer_info* out);
+
+/* Copy the sorted Hilbert keys of a built layer (which = 0: objects, 1:
+ * polygon boxes) into `out` (device memory, n entries, n = objects / polygons). */
+int hv_layer_keys(hv_layer* layer, int which, uint64_t* out, uint64_t n);
+
+/* lower_bound of each query key in the sorted keys through the learned model
+ * (which = 0: objects, 1: polygon boxes): keys and out are device arrays of n
+ * entries; *fallbacks receives how many lookups left the model's error window
+ * and were answered by a full binary search.  Synchronises `stream`. */
+int hv_learned_lookup(hv_layer* layer, int which, const uint64_t* keys, uint32_t n, uint64_t* out,
+                      uint64_t* fallbacks, void* stream);
 int hv_layer_free(hv_layer* layer);
 
 /* Write / read a built layer (objects, R-tree, learned model) to / from a

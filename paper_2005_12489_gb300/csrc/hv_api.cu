@@ -323,6 +323,15 @@ int hv_layer_info_get(hv_layer* layer, hv_layer_info* out) {
     out->learned_outliers = L->learned.n_outliers;
     out->build_ms = L->build_ms;
     out->train_ms = L->learned.train_ms + L->mbr_learned.train_ms;
+    const LearnedView& lv = L->learned.view;
+    if (lv.ready) {
+        out->learned_error_linear = lv.eps_linear;
+        out->learned_error_mlp = lv.eps_mlp;
+        out->learned_mean_error = lv.mean_err;
+        out->learned_pieces = lv.n_seg;
+        out->learned_mlp = lv.hidden > 0 ? 1u : 0u;
+        out->learned_halo = lv.halo;
+    }
     uint64_t bytes = L->obj_bytes + (L->keys ? L->n_obj * 8 : 0) + L->tree.nodes_bytes;
     if (L->kind == HV_LAYER_POLYGONS)
         bytes += L->n_obj * 16 + (L->n_poly + 1) * 8 + L->n_poly * (16 + 4 + 8) + L->mbr_tree.nodes_bytes;
@@ -394,6 +403,30 @@ int hv_render_tiles(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mo
     // the scratch copies above must finish before the next call reuses them
     HV_CUDA(cudaStreamSynchronize(st));
     return HV_OK;
+}
+
+int hv_layer_keys(hv_layer* layer, int which, uint64_t* out, uint64_t n) {
+    if (!layer || !out) { set_error("hv_layer_keys: NULL argument"); return HV_EINVAL; }
+    Layer* L = (Layer*)layer;
+    if (!(L->indexes & HV_INDEX_RTREE)) { set_error("hv_layer_keys: index not built"); return HV_ESTATE; }
+    const uint64_t* k = which == 0 ? L->keys : L->mbr_keys;
+    uint64_t cnt = which == 0 ? L->n_obj : (L->kind == HV_LAYER_POLYGONS ? L->n_poly : 0);
+    if (which != 0 && which != 1) { set_error("hv_layer_keys: which must be 0 or 1"); return HV_EINVAL; }
+    if (n != cnt) { set_error("hv_layer_keys: n must be %llu", (unsigned long long)cnt); return HV_EINVAL; }
+    if (!is_device_ptr(out)) { set_error("hv_layer_keys: out must be device memory"); return HV_EINVAL; }
+    HV_CUDA(cudaSetDevice(L->ctx->device));
+    if (cnt) HV_CUDA(cudaMemcpy(out, k, cnt * 8, cudaMemcpyDeviceToDevice));
+    return HV_OK;
+}
+
+int hv_learned_lookup(hv_layer* layer, int which, const uint64_t* keys, uint32_t n, uint64_t* out,
+                      uint64_t* fallbacks, void* stream) {
+    if (!layer || (!keys && n) || (!out && n) || !fallbacks) { set_error("hv_learned_lookup: NULL argument"); return HV_EINVAL; }
+    if (which != 0 && which != 1) { set_error("hv_learned_lookup: which must be 0 or 1"); return HV_EINVAL; }
+    Layer* L = (Layer*)layer;
+    if (n && (!is_device_ptr(keys) || !is_device_ptr(out))) { set_error("hv_learned_lookup: device arrays required"); return HV_EINVAL; }
+    HV_CUDA(cudaSetDevice(L->ctx->device));
+    return learned_lookup(L, which, keys, n, out, fallbacks, (cudaStream_t)stream);
 }
 
 int hv_render_tiles_counted(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode,

@@ -295,6 +295,27 @@ int build_tree_polygons(Layer* L) {
     return HV_OK;
 }
 
+// A side R-tree over `n` boxes or segments (the learned index's long
+// objects), with the ids carried along; takes ownership of objs and ids.
+int build_side_tree(Ctx* c, int4* objs, uint32_t* ids, uint64_t n, Tree* t, int4** sorted_objs,
+                    uint32_t** sorted_ids) {
+    uint64_t* keys = nullptr;
+    uint32_t* perm = nullptr;
+    HV_TRY(sort_objects<SegObj>(c, &objs, n, &keys, &perm));
+    // ids follow the sort
+    uint32_t* sid;
+    HV_TRY(dev_alloc(c, (void**)&sid, n * 4));
+    k_gather<uint32_t><<<grid_for(n, 256), 256>>>(ids, perm, n, sid);
+    HV_CUDA(cudaDeviceSynchronize());
+    dev_free(c, ids, n * 4);
+    dev_free(c, perm, n * 4);
+    dev_free(c, keys, n * 8);
+    HV_TRY(build_levels<SegObj>(c, objs, n, t));
+    *sorted_objs = objs;
+    *sorted_ids = sid;
+    return HV_OK;
+}
+
 // ---- A0: layer preparation on the device (used by hv_api.cu) ---------------
 
 int prepare_lines(Ctx* c, const int2* d_xy, uint64_t n_vert, const uint64_t* h_line_off,

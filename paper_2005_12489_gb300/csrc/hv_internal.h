@@ -59,24 +59,32 @@ struct Tree {
     uint64_t n_nodes = 0;
 };
 
-// Learned position index over the sorted Hilbert keys of a tree's objects.
+// Learned position index over the sorted Hilbert keys of a tree's objects
+// (model layout in hv_learned.cuh).
 struct LearnedView {
     const uint64_t* keys = nullptr;     // sorted keys, n_obj
-    const float* seg_a = nullptr;       // per piece: slope, intercept (positions)
-    const float* seg_b = nullptr;
     const uint64_t* seg_k0 = nullptr;   // first key of each piece
+    const float* seg_a = nullptr;       // slope of each piece
+    const float* seg_b = nullptr;       // intercept of each piece
+    const float* pinv = nullptr;        // 1 / key span of each piece
+    const uint32_t* eps_piece = nullptr;  // per-piece position error bound
     const uint32_t* radix = nullptr;    // top-bits table -> first piece
-    const uint16_t* mlp = nullptr;      // bf16 weights, packed (see hv_learned.cu)
+    const uint16_t* mlp = nullptr;      // bf16 MLP weights (NULL: linear only)
+    const uint16_t* emb = nullptr;      // bf16 piece embeddings
     uint32_t n_seg = 0;
-    uint32_t radix_bits = 0;
-    uint32_t hidden = 0;
+    uint32_t P = 0;                     // keys per piece
+    int hidden = 0;                     // MLP width, 0 = not used
     int64_t eps = 0;                    // max position error of the model
+    int64_t eps_linear = 0;             // ... of the linear pieces alone
+    int64_t eps_mlp = 0;                // ... with the MLP residual
+    double mean_err = 0;
     int32_t halo = 0;                   // max half-extent of indexed objects
     uint64_t n_obj = 0;
-    // objects whose extent exceeds `halo` are kept out of the key ranges and
-    // are found through their own small R-tree
+    // objects whose extent exceeds `halo` are also kept in a small side
+    // R-tree that every lookup searches
     TreeView outliers;
-    const void* outlier_obj = nullptr;
+    const int4* outlier_obj = nullptr;
+    const uint32_t* outlier_ids = nullptr;
     bool ready = false;
 };
 
@@ -122,6 +130,8 @@ void free_tree(Ctx* c, Tree* t);
 // learned index (hv_learned.cu)
 int build_learned(Layer* L, const hv_build_opts* opts);
 void free_learned(Ctx* c, Learned* l);
+int learned_lookup(Layer* L, int which, const uint64_t* q, uint32_t n, uint64_t* out, uint64_t* fallbacks,
+                   cudaStream_t st);
 // render (hv_render.cu)
 struct RenderLog {
     int64_t* log;

@@ -22,6 +22,7 @@
 // COVERAGE bytes or RGBA) with coalesced 16-byte stores.
 #include "hv_device.cuh"
 #include "hv_internal.h"
+#include "hv_learned.cuh"
 
 namespace hv {
 
@@ -64,6 +65,16 @@ struct Params {
     const int4* poly_edges;
     const uint64_t* poly_edge_off;
     uint32_t* status;
+    // learned candidate lookup (use_learned): models over the sorted keys of
+    // the objects and of the polygon boxes, their halos and side trees
+    int use_learned;
+    LModel lm, mlm;
+    int32_t halo, mhalo;
+    TreeArg side, mside;
+    const void* side_obj;
+    const uint32_t* side_ids;
+    const int4* mside_obj;
+    const uint32_t* mside_ids;
     // instrumentation (NULL in normal use): every node, leaf and polygon read
     // is appended as (tile << 38 | kind << 35 | id)
     unsigned long long* log;
@@ -86,11 +97,21 @@ struct Smem {
     uint8_t res[kStripRows * kTile];
     int4 fbox[2][kFCap];
     uint32_t fid[2][kFCap];
-    const int32_t* lvl_base[kMaxLevels + 1];
+    const int32_t* lvl_base[2][kMaxLevels + 1];   // [0]: tree being traversed, [1]: its side tree
     uint32_t stk_node[kWarps][kMaxLevels + 1];
     uint32_t stk_mask[kWarps][kMaxLevels + 1];
     uint32_t lanemask[kWarps][kMaxLevels + 1][32];
     int f_count, f_level, f_buf, next_count, next_block;
+};
+
+// Where a traversal reads its objects: a tree's sorted objects (with polygon
+// ids for polygon boxes) and the per-level node bases in shared memory.
+struct Src {
+    const void* obj;
+    const uint32_t* ids;
+    uint64_t n;
+    const int32_t* nodes;        // node array (for the read log)
+    const int32_t* const* lvl;   // lvl[l] = first node of level l
 };
 
 // Per-lane state of one 8 x 4 pixel block (lane l = pixel (l & 7, l >> 3)).
@@ -192,11 +213,11 @@ __device__ __forceinline__ bool reaches(const Lane& s, bool fill, uint32_t cm, i
 
 struct PointLeaf {
     static constexpr bool kFill = false;
-    __device__ static void visit(const Params& p, uint32_t leaf, Lane& s, int lane) {
+    __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         uint64_t i = (uint64_t)leaf * 32 + lane;
         log_read(p, kLogLeaf, leaf, lane);
         int2 o = make_int2(kEmptyHi, kEmptyHi);
-        if (i < p.tree.n_obj) o = __ldg((const int2*)p.obj + i);
+        if (i < src.n) o = __ldg((const int2*)src.obj + i);
         uint32_t pm = rect_lanes(s, o.x, o.y, o.x, o.y) & s.U;
         if (!__any_sync(kFull, pm != 0)) return;
         const int32_t ps = 1 << s.L;
@@ -220,11 +241,11 @@ struct PointLeaf {
 
 struct SegLeaf {
     static constexpr bool kFill = false;
-    __device__ static void visit(const Params& p, uint32_t leaf, Lane& s, int lane) {
+    __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         uint64_t i = (uint64_t)leaf * 32 + lane;
         log_read(p, kLogLeaf, leaf, lane);
         int4 o = make_int4(kEmptyHi, kEmptyHi, kEmptyHi, kEmptyHi);
-        if (i < p.tree.n_obj) o = __ldg((const int4*)p.obj + i);
+        if (i < src.n) o = __ldg((const int4*)src.obj + i);
         const int32_t sx0 = min(o.x, o.z), sy0 = min(o.y, o.w), sx1 = max(o.x, o.z), sy1 = max(o.y, o.w);
         uint32_t pm = rect_lanes(s, sx0, sy0, sx1, sy1) & s.U;
         if (!__any_sync(kFull, pm != 0)) return;
@@ -251,14 +272,14 @@ struct SegLeaf {
 // unfilled pixel centre, count that polygon's own edges crossing the ray.
 struct FillLeaf {
     static constexpr bool kFill = true;
-    __device__ static void visit(const Params& p, uint32_t leaf, Lane& s, int lane) {
+    __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         uint64_t i = (uint64_t)leaf * 32 + lane;
         log_read(p, kLogPolyLeaf, leaf, lane);
         int4 b = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
         uint32_t id = 0;
-        if (i < p.mtree.n_obj) {
-            b = __ldg(p.mbr_obj + i);
-            id = __ldg(p.mbr_ids + i);
+        if (i < src.n) {
+            b = __ldg((const int4*)src.obj + i);
+            id = __ldg(src.ids + i);
         }
         uint32_t pm = rect_lanes(s, b.x, b.y, b.z, b.w);
         uint32_t m = __ballot_sync(kFull, (pm & s.U) != 0);
@@ -296,11 +317,10 @@ struct FillLeaf {
 
 // Child boxes of one inner node: lane c computes the lanes child c can
 // reach, keeps it in `lm`, and the ballot selects the children to visit.
-__device__ __forceinline__ uint32_t child_hits(const Params& p, bool fill, const int32_t* base,
-                                               const Lane& s, int lane, uint32_t* lm) {
+__device__ __forceinline__ uint32_t child_hits(const Params& p, bool fill, const Src& src,
+                                               const int32_t* base, const Lane& s, int lane, uint32_t* lm) {
     if (p.log != nullptr)
-        log_read(p, fill ? kLogPolyNode : kLogNode,
-                 (uint64_t)(base - (fill ? p.mtree.nodes : p.tree.nodes)) >> 7, lane);
+        log_read(p, fill ? kLogPolyNode : kLogNode, (uint64_t)(base - src.nodes) >> 7, lane);
     int32_t x0 = __ldg(base + lane), y0 = __ldg(base + 32 + lane);
     int32_t x1 = __ldg(base + 64 + lane), y1 = __ldg(base + 96 + lane);
     uint32_t cm = rect_lanes(s, x0, y0, x1, y1);
@@ -313,11 +333,12 @@ __device__ __forceinline__ uint32_t child_hits(const Params& p, bool fill, const
 // still to visit, and each child's lane reach (re-tested against the
 // shrinking undecided set before every visit).
 template <class V>
-__device__ void descend(const Params& p, Smem& sm, int level, uint32_t node, Lane& s, int lane, int warp) {
+__device__ void descend(const Params& p, Smem& sm, const Src& src, int level, uint32_t node, Lane& s,
+                        int lane, int warp) {
     uint32_t* stk_node = sm.stk_node[warp];
     uint32_t* stk_mask = sm.stk_mask[warp];
     int lvl = level;
-    uint32_t m0 = child_hits(p, V::kFill, sm.lvl_base[lvl] + (uint64_t)node * 128, s, lane,
+    uint32_t m0 = child_hits(p, V::kFill, src, src.lvl[lvl] + (uint64_t)node * 128, s, lane,
                              sm.lanemask[warp][lvl]);
     stk_node[lvl] = node;
     stk_mask[lvl] = m0;
@@ -336,11 +357,11 @@ __device__ void descend(const Params& p, Smem& sm, int level, uint32_t node, Lan
         stk_mask[lvl] = m & (m - 1);
         __syncwarp();
         if (lvl == 1) {
-            V::visit(p, child, s, lane);
+            V::visit(p, src, child, s, lane);
             if (s.U == 0) return;
         } else {
             lvl--;
-            uint32_t hm = child_hits(p, V::kFill, sm.lvl_base[lvl] + (uint64_t)child * 128, s, lane,
+            uint32_t hm = child_hits(p, V::kFill, src, src.lvl[lvl] + (uint64_t)child * 128, s, lane,
                                      sm.lanemask[warp][lvl]);
             stk_node[lvl] = child;
             stk_mask[lvl] = hm;
@@ -353,9 +374,6 @@ __device__ void descend(const Params& p, Smem& sm, int level, uint32_t node, Lan
 __device__ void cull(const Params& p, const TreeArg& t, bool fill, Smem& sm, int32_t x0, int32_t y0,
                      int32_t x1, int32_t y1, int tid) {
     int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int l = 0; l <= kMaxLevels; l++)
-        if (tid == l) sm.lvl_base[l] = (l >= 1 && l <= t.top) ? t.nodes + t.level_off[l] * 128 : nullptr;
     if (tid == 0) {
         sm.f_buf = 0;
         sm.f_level = t.top;
@@ -372,7 +390,7 @@ __device__ void cull(const Params& p, const TreeArg& t, bool fill, Smem& sm, int
         int cur = sm.f_buf, lvl = sm.f_level, cnt = sm.f_count;
         if (tid == 0) sm.next_count = 0;
         __syncthreads();
-        const int32_t* base = sm.lvl_base[lvl];
+        const int32_t* base = sm.lvl_base[0][lvl];
         for (int e = warp; e < cnt; e += kWarps) {
             uint32_t node = sm.fid[cur][e];
             const int32_t* nd = base + (uint64_t)node * 128;
@@ -406,10 +424,104 @@ __device__ void cull(const Params& p, const TreeArg& t, bool fill, Smem& sm, int
     }
 }
 
-// Process every pixel block of the strip against the current frontier.
+// Level bases of a tree into shared memory slot `slot` (0: the tree being
+// traversed, 1: its side tree).
+__device__ __forceinline__ void set_levels(Smem& sm, int slot, const TreeArg& t, int tid) {
+#pragma unroll
+    for (int l = 0; l <= kMaxLevels; l++)
+        if (tid == l) sm.lvl_base[slot][l] = (l >= 1 && l <= t.top) ? t.nodes + t.level_off[l] * 128 : nullptr;
+}
+
+// Visit the R-tree subtrees that span sorted positions [lo, hi): the leaf
+// range is split into maximal aligned subtrees, whose boxes (stored in their
+// parent nodes) are tested before each visit.
 template <class V>
-__device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, int strip, int z,
-                            int32_t R, bool mask_mode, int tid) {
+__device__ void visit_range(const Params& p, Smem& sm, const Src& src, int top, uint64_t lo, uint64_t hi, Lane& s,
+                            int lane, int warp) {
+    uint64_t a = lo >> 5, b = (hi - 1) >> 5;
+    while (a <= b && s.U) {
+        int l = 0;
+        while (l + 1 < top && (a & ((1ull << (5 * (l + 1))) - 1)) == 0 && a + (1ull << (5 * (l + 1))) - 1 <= b) l++;
+        const int32_t* par = src.lvl[l + 1] + (a >> (5 * (l + 1))) * 128;
+        int c = (int)((a >> (5 * l)) & 31);
+        int32_t x0 = __ldg(par + c), y0 = __ldg(par + 32 + c), x1 = __ldg(par + 64 + c), y1 = __ldg(par + 96 + c);
+        if (reaches(s, V::kFill, rect_lanes(s, x0, y0, x1, y1), x0, y0, x1, y1)) {
+            if (l == 0)
+                V::visit(p, src, (uint32_t)a, s, lane);
+            else
+                descend<V>(p, sm, src, l, (uint32_t)(a >> (5 * l)), s, lane, warp);
+        }
+        a += 1ull << (5 * l);
+    }
+}
+
+// Learned candidate lookup for one block: cover the reach of the block's
+// undecided samples, widened by the halo of object extents, with at most 32
+// aligned Hilbert cells (the cells' key ranges are contiguous runs of the
+// sorted order); find each cell's position range through the model; visit
+// the R-tree subtrees spanning those positions; then search the side tree of
+// objects longer than the halo.
+template <class V>
+__device__ void learned_block(const Params& p, Smem& sm, const Src& src, const Src& side, int top, int side_top,
+                              const LModel& m, int32_t halo, Lane& s, int lane, int warp) {
+    int32_t ux0 = kEmptyLo, uy0 = kEmptyLo, ux1 = kEmptyHi, uy1 = kEmptyHi;
+    if (s.und) {
+        ux0 = s.cx - s.off; ux1 = s.cx + s.off;
+        uy0 = s.cy - s.off; uy1 = s.cy + s.off;
+    }
+    ux0 = __reduce_min_sync(kFull, ux0);
+    uy0 = __reduce_min_sync(kFull, uy0);
+    ux1 = __reduce_max_sync(kFull, ux1);
+    uy1 = __reduce_max_sync(kFull, uy1);
+    const int64_t e = (int64_t)(s.ext - s.off) + halo;
+    const int64_t lo_g = -(int64_t)kGridHalf, hi_g = (int64_t)kGridHalf - 1;
+    int64_t qx0 = max((int64_t)ux0 - e, lo_g), qx1 = min((int64_t)ux1 + e, hi_g);
+    int64_t qy0 = max((int64_t)uy0 - e, lo_g), qy1 = min((int64_t)uy1 + e, hi_g);
+    if (m.n > 0 && qx0 <= qx1 && qy0 <= qy1) {
+        const int64_t W = qx1 - qx0 + 1, Hh = qy1 - qy0 + 1;
+        int k = 0;
+        while (k < 31 && (((int64_t)7 << k) < W || ((int64_t)3 << k) < Hh)) k++;
+        const int64_t gx0 = (qx0 + kGridHalf) >> k, gx1 = (qx1 + kGridHalf) >> k;
+        const int64_t gy0 = (qy0 + kGridHalf) >> k, gy1 = (qy1 + kGridHalf) >> k;
+        const int nx = (int)(gx1 - gx0 + 1), ny = (int)(gy1 - gy0 + 1);
+        int32_t cx0 = 0, cy0 = 0, cx1 = 0, cy1 = 0;
+        bool active = false;
+        uint64_t plo = 0, phi = 0;
+        if (lane < nx * ny) {
+            int64_t gx = gx0 + lane % nx, gy = gy0 + lane / nx;
+            int64_t x0 = (gx << k) - kGridHalf, y0 = (gy << k) - kGridHalf;
+            int64_t x1 = x0 + ((int64_t)1 << k) - 1, y1 = y0 + ((int64_t)1 << k) - 1;
+            // objects whose centre lies in the cell lie within the cell +- halo
+            cx0 = (int32_t)max(x0 - halo, lo_g); cy0 = (int32_t)max(y0 - halo, lo_g);
+            cx1 = (int32_t)min(x1 + halo, hi_g); cy1 = (int32_t)min(y1 + halo, hi_g);
+            active = reaches(s, V::kFill, rect_lanes(s, cx0, cy0, cx1, cy1), cx0, cy0, cx1, cy1);
+            if (active) {
+                uint64_t span = (k >= 31) ? (1ull << 62) : (1ull << (2 * k));
+                uint64_t klo = (k >= 31) ? 0ull : (hilbert_key((int32_t)x0, (int32_t)y0) & ~(span - 1));
+                bool fb;
+                plo = learn_lower_bound(m, klo, &fb);
+                phi = learn_lower_bound(m, klo + span, &fb);
+            }
+        }
+        uint32_t cm = __ballot_sync(kFull, active && phi > plo);
+        while (cm && s.U) {
+            int c = __ffs(cm) - 1;
+            cm &= cm - 1;
+            uint64_t a = __shfl_sync(kFull, plo, c), b = __shfl_sync(kFull, phi, c);
+            visit_range<V>(p, sm, src, top, a, b, s, lane, warp);
+            cm &= __ballot_sync(kFull, ((cm >> lane) & 1u) &&
+                                           reaches(s, V::kFill, rect_lanes(s, cx0, cy0, cx1, cy1), cx0, cy0, cx1, cy1));
+        }
+    }
+    if (s.U && side_top > 0) descend<V>(p, sm, side, side_top, 0, s, lane, warp);
+}
+
+// Process every pixel block of the strip: against the culled frontier (R-tree)
+// or through the learned lookup.
+template <class V>
+__device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src& side, int top, int side_top,
+                            const LModel* m, int32_t halo, int32_t X0, int32_t Y0, int strip, int z, int32_t R,
+                            bool mask_mode, int tid) {
     int lane = tid & 31, warp = tid >> 5;
     const int L = 23 - z;
     const int32_t ps = 1 << L;
@@ -443,26 +555,31 @@ __device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, i
         s.U = kFull;
         for (int k = 0; k < 4; k++) s.Uk[k] = k < s.nk ? kFull : 0u;
         uint32_t und0 = s.und;
-        for (int c0 = 0; c0 < f_count && s.U; c0 += 32) {
-            int e = c0 + lane;
-            uint32_t cm = 0;
-            int4 fbx = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
-            if (e < f_count) {
-                fbx = sm.fbox[fb][e];
-                cm = rect_lanes(s, fbx.x, fbx.y, fbx.z, fbx.w);
-            }
-            uint32_t m = __ballot_sync(kFull, reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
-            while (m) {
-                int k = __ffs(m) - 1;
-                m &= m - 1;
-                uint32_t id = sm.fid[fb][c0 + k];
-                if (f_level == 0) {
-                    V::visit(p, id, s, lane);
-                } else {
-                    descend<V>(p, sm, f_level, id, s, lane, warp);
+        if (m != nullptr) {
+            learned_block<V>(p, sm, src, side, top, side_top, *m, halo, s, lane, warp);
+        } else {
+            for (int c0 = 0; c0 < f_count && s.U; c0 += 32) {
+                int e = c0 + lane;
+                uint32_t cm = 0;
+                int4 fbx = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
+                if (e < f_count) {
+                    fbx = sm.fbox[fb][e];
+                    cm = rect_lanes(s, fbx.x, fbx.y, fbx.z, fbx.w);
                 }
-                // drop frontier entries that no longer reach an undecided lane
-                m &= __ballot_sync(kFull, ((m >> lane) & 1u) && reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
+                uint32_t mm = __ballot_sync(kFull, reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
+                while (mm) {
+                    int k = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    uint32_t id = sm.fid[fb][c0 + k];
+                    if (f_level == 0) {
+                        V::visit(p, src, id, s, lane);
+                    } else {
+                        descend<V>(p, sm, src, f_level, id, s, lane, warp);
+                    }
+                    // drop frontier entries that no longer reach an undecided lane
+                    mm &= __ballot_sync(kFull, ((mm >> lane) & 1u) &&
+                                                   reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
+                }
             }
         }
         uint32_t covered = und0 & ~s.und;
@@ -476,6 +593,35 @@ __device__ void blocks_pass(const Params& p, Smem& sm, int32_t X0, int32_t Y0, i
         }
         sm.res[jl * kTile + i] = r;
     }
+}
+
+// One stage (Algorithm 1 over points / segments / edges, or Algorithm 2 over
+// polygon boxes) for the strip: cull (R-tree) or check the layer box
+// (learned), then every block.
+template <class V>
+__device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* obj, const uint32_t* ids,
+                      const TreeArg& st, const void* sobj, const uint32_t* sids, const LModel* m, int32_t halo,
+                      int32_t X0, int32_t Y0, int strip, int z, int32_t R, bool mask_mode, int32_t bx0, int32_t by0,
+                      int32_t bx1, int32_t by1, int tid) {
+    set_levels(sm, 0, t, tid);
+    set_levels(sm, 1, st, tid);
+    if (tid == 0) sm.next_block = 0;
+    __syncthreads();
+    bool any;
+    if (m == nullptr) {
+        cull(p, t, V::kFill, sm, bx0, by0, bx1, by1, tid);
+        any = sm.f_count > 0;
+    } else {
+        int4 rb = t.root_box, sb = st.root_box;
+        any = (t.top > 0 && rb.x <= bx1 && rb.z >= bx0 && rb.y <= by1 && rb.w >= by0) ||
+              (st.top > 0 && sb.x <= bx1 && sb.z >= bx0 && sb.y <= by1 && sb.w >= by0);
+    }
+    if (any) {
+        Src src{obj, ids, t.n_obj, t.nodes, sm.lvl_base[0]};
+        Src side{sobj, sids, st.n_obj, st.nodes, sm.lvl_base[1]};
+        blocks_pass<V>(p, sm, src, side, t.top, st.top, m, halo, X0, Y0, strip, z, R, mask_mode, tid);
+    }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
@@ -503,27 +649,22 @@ __global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
         const int32_t sx0 = X0 + (ps >> 1) - off, sx1 = X0 + (kTile - 1) * ps + (ps >> 1) + off;
         const int32_t sy0 = Y0 + strip * kStripRows * ps + (ps >> 1) - off;
         const int32_t sy1 = Y0 + (strip * kStripRows + kStripRows - 1) * ps + (ps >> 1) + off;
+        const bool learned = p.use_learned != 0;
         // Algorithm 1 over points / segments / polygon edges
-        cull(p, p.tree, false, sm, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
-        if (tid == 0) sm.next_block = 0;
-        __syncthreads();
-        if (sm.f_count > 0) {
-            if (p.kind == HV_LAYER_POINTS)
-                blocks_pass<PointLeaf>(p, sm, X0, Y0, strip, z, R, mask_mode, tid);
-            else
-                blocks_pass<SegLeaf>(p, sm, X0, Y0, strip, z, R, mask_mode, tid);
-        }
-        __syncthreads();
+        if (p.kind == HV_LAYER_POINTS)
+            stage<PointLeaf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
+                             p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
+        else
+            stage<SegLeaf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
+                           p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
         // Algorithm 2 over polygon boxes and edges
         if (p.kind == HV_LAYER_POLYGONS) {
             const int32_t cx0 = X0 + (ps >> 1), cx1 = X0 + (kTile - 1) * ps + (ps >> 1);
             const int32_t cy0 = Y0 + strip * kStripRows * ps + (ps >> 1);
             const int32_t cy1 = Y0 + (strip * kStripRows + kStripRows - 1) * ps + (ps >> 1);
-            cull(p, p.mtree, true, sm, cx0, cy0, cx1, cy1, tid);
-            if (tid == 0) sm.next_block = 0;
-            __syncthreads();
-            if (sm.f_count > 0) blocks_pass<FillLeaf>(p, sm, X0, Y0, strip, z, 0, mask_mode, tid);
-            __syncthreads();
+            stage<FillLeaf>(p, sm, p.mtree, p.mbr_obj, p.mbr_ids, p.mside, p.mside_obj, p.mside_ids,
+                            learned ? &p.mlm : nullptr, p.mhalo, X0, Y0, strip, z, 0, mask_mode, cx0, cy0, cx1,
+                            cy1, tid);
         }
     }
     // ---- encode the strip (Sec. 4.1 Render Tiles) ----
@@ -589,6 +730,8 @@ TreeArg tree_arg(const TreeView& v) {
 
 }  // namespace
 
+LModel learned_model(const LearnedView& v);
+
 uint32_t render_launch_count(Layer*, int) { return 1; }
 
 int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int index_kind,
@@ -615,6 +758,27 @@ int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int
     p.poly_edges = L->poly_edges;
     p.poly_edge_off = L->poly_edge_off;
     p.status = L->status;
+    if (index_kind == HV_INDEX_LEARNED) {
+        const LearnedView& a = L->learned.view;
+        const LearnedView& b = L->mbr_learned.view;
+        if (!a.ready || (L->kind == HV_LAYER_POLYGONS && !b.ready)) {
+            set_error("learned index not built");
+            return HV_ESTATE;
+        }
+        p.use_learned = 1;
+        p.lm = learned_model(a);
+        p.halo = a.halo;
+        p.side = tree_arg(a.outliers);
+        p.side_obj = a.outlier_obj;
+        p.side_ids = a.outlier_ids;
+        if (L->kind == HV_LAYER_POLYGONS) {
+            p.mlm = learned_model(b);
+            p.mhalo = b.halo;
+            p.mside = tree_arg(b.outliers);
+            p.mside_obj = b.outlier_obj;
+            p.mside_ids = b.outlier_ids;
+        }
+    }
     if (log) {
         p.log = (unsigned long long*)log->log;
         p.log_cap = log->cap;

@@ -51,7 +51,11 @@ class hv_layer_info(ctypes.Structure):
                 ("mbr", ctypes.c_int32 * 4), ("tree_levels", ctypes.c_uint32),
                 ("tree_nodes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("learned_error", ctypes.c_int64), ("learned_outliers", ctypes.c_uint64),
-                ("build_ms", ctypes.c_double), ("train_ms", ctypes.c_double)]
+                ("build_ms", ctypes.c_double), ("train_ms", ctypes.c_double),
+                ("learned_error_linear", ctypes.c_int64), ("learned_error_mlp", ctypes.c_int64),
+                ("learned_mean_error", ctypes.c_double), ("learned_pieces", ctypes.c_uint32),
+                ("learned_mlp", ctypes.c_uint32), ("learned_halo", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class hv_server_opts(ctypes.Structure):
@@ -82,6 +86,8 @@ SIGNATURES = {
     "hv_layer_load_polygons": [P, P, U64, P, U64, P, U64, ctypes.POINTER(P)],
     "hv_layer_build_index": [P, U32, P],
     "hv_layer_info_get": [P, ctypes.POINTER(hv_layer_info)],
+    "hv_layer_keys": [P, I32, P, U64],
+    "hv_learned_lookup": [P, I32, P, U32, P, ctypes.POINTER(U64), P],
     "hv_layer_free": [P],
     "hv_layer_save": [P, ctypes.c_char_p],
     "hv_layer_load_file": [P, ctypes.c_char_p, ctypes.POINTER(P)],
@@ -211,6 +217,23 @@ def hv_layer_info_get(layer):
     info = hv_layer_info()
     _check(lib().hv_layer_info_get(layer, ctypes.byref(info)))
     return info
+
+
+def hv_layer_keys(layer, which, out, n):
+    _check(lib().hv_layer_keys(layer, which, ptr(out), n))
+
+
+def hv_learned_lookup(layer, which, keys, n, out, stream=None):
+    """Returns the number of lookups answered by the full-search fallback."""
+    fb = U64()
+    _check(lib().hv_learned_lookup(layer, which, ptr(keys), n, ptr(out), ctypes.byref(fb),
+                                   stream_handle(stream)))
+    return fb.value
+
+
+def info_dict(layer):
+    i = hv_layer_info_get(layer)
+    return {name: (list(getattr(i, name)) if name == "mbr" else getattr(i, name)) for name, _ in i._fields_}
 
 
 def hv_layer_free(layer):
