@@ -51,8 +51,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4],
-                    help="2: clustered points (the headline), 3: linestrings, 4: polygons")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
+                    help="2: clustered points (the headline), 3: linestrings, 4: polygons, "
+                         "5: serving an open-loop request stream over resident layers")
+    ap.add_argument("--rates", default="5000,10000,20000,50000,inf",
+                    help="config 5: request rates (tiles/s), 'inf' = all at once")
+    ap.add_argument("--requests", type=int, default=40_000, help="config 5: requests per rate")
+    ap.add_argument("--serve-points", type=int, default=1_000_000_000)
+    ap.add_argument("--serve-segments", type=int, default=200_000_000)
     ap.add_argument("--r16", type=int, default=None)
     ap.add_argument("--points", type=int, default=None, help="objects (points / segments / polygons)")
     ap.add_argument("--tiles", type=int, default=WORKLOAD["tiles_per_step"])
@@ -426,10 +432,80 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
+def run_serving(args):
+    """Open-loop serving over resident layers (HiVision Exp. 3 shape):
+    clustered points + random-walk segments, requests from pan/zoom sessions
+    (Zipf start tiles, mixed zoom 2-18, layer 50/50, r16 16-48, RGBA), Poisson
+    arrivals at each rate; per rate: achieved tiles/s and p50/p99 latency
+    (completion - scheduled arrival)."""
+    import torch
+    from paper_2005_12489_gb300 import hv
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    t0 = time.time()
+    pts = gen.gmm_points(args.serve_points, seed=5, k=64)
+    n_lines = max(1, args.serve_segments // 10)
+    xy, off = gen.walk_lines(n_lines, args.serve_segments, seed=55)
+    gen_s = time.time() - t0
+    ctx = hv.hv_create(local)
+    layers = [hv.hv_layer_load_points(ctx, pts), hv.hv_layer_load_linestrings(ctx, xy, off)]
+    t1 = time.time()
+    for L in layers:
+        hv.hv_layer_build_index(L, hv.HV_INDEX_RTREE | hv.HV_INDEX_LEARNED)
+    build_s = time.time() - t1
+    anchors = [pts[:: max(1, len(pts) // 2_000_000)], gen.segment_midpoints(xy, off, 2_000_000, seed=56)]
+    del pts, xy, off
+    style = hv.make_style(STYLE_T[:3], STYLE_T[4:7])
+    results = []
+    for ri, rate in enumerate(args.rates.split(",")):
+        tr = gen.pan_zoom_trace(anchors, args.requests, seed=500 + ri)
+        reqs = np.zeros(len(tr), dtype=hv.REQ_DTYPE)
+        reqs["z"], reqs["x"], reqs["y"], reqs["r16"], reqs["layer"] = tr[:, 0], tr[:, 1], tr[:, 2], tr[:, 3], tr[:, 4]
+        reqs["mode"] = hv.HV_MODE_RGBA
+        if rate == "inf":
+            arrival = np.zeros(len(reqs))
+        else:
+            arrival = gen.poisson_arrivals(len(reqs), float(rate), seed=600 + ri)
+        for index in (hv.HV_INDEX_LEARNED, hv.HV_INDEX_RTREE):
+            opts = hv.make_server_opts(max_batch=64, queue_capacity=1 << 20, scratch_bytes=4 << 30,
+                                       index_kind=index, use_graphs=1, style=style)
+            srv = hv.hv_server_start(ctx, layers, opts)
+            try:
+                lat, wall = hv.hv_server_replay(srv, reqs, arrival)
+                st = hv.hv_server_stats(srv)
+            finally:
+                hv.hv_server_stop(srv)
+            results.append({"rate": rate, "index": "learned" if index == hv.HV_INDEX_LEARNED else "rtree",
+                            "tiles_per_s": len(reqs) / (wall / 1e6),
+                            "p50_ms": float(np.percentile(lat, 50)) / 1000,
+                            "p99_ms": float(np.percentile(lat, 99)) / 1000,
+                            "mean_batch": st["tiles"] / max(1, st["batches"]), "slots": st["slots"],
+                            "graph_launches": st["graph_launches"]})
+            print(json.dumps(results[-1]), file=sys.stderr, flush=True)
+    infos = [hv.info_dict(L) for L in layers]
+    best = max(r["tiles_per_s"] for r in results if r["index"] == "learned")
+    line = {"metric": "served tiles/s and p50/p99 tile latency, open-loop request stream, 1 GB300",
+            "value": best, "unit": "tiles/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "resident layers: %d clustered points + %d random-walk segments; "
+                                   "pan/zoom session requests (Zipf start tiles, zoom 2-18, layer 50/50, "
+                                   "r16 16-48, RGBA), Poisson arrivals" % (args.serve_points, args.serve_segments),
+                       "requests_per_rate": args.requests, "max_batch": 64, "graphs": True},
+            "per_rate": results, "generate_s": gen_s, "index_build_s": build_s,
+            "layers": [{k: v for k, v in i.items() if k in ("n_objects", "learned_error", "learned_outliers",
+                                                           "train_ms", "build_ms", "device_bytes")} for i in infos]}
+    print(json.dumps(line), flush=True)
+    for L in layers:
+        hv.hv_layer_free(L)
+    hv.hv_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == 5:
+        run_serving(args)
     else:
         run_gb300(args)
 

@@ -243,28 +243,59 @@ int hv_render_launches(hv_layer* layer, int index_kind, uint32_t* launches);
 
 /* ---- serving (Sec. 4: MTVS task pool, IMMF, HPVE as one GPU loop) ------ */
 
+/* A native worker thread keeps the layers resident and serves tile requests
+ * of mixed layer, zoom, radius and mode as they arrive: requests wait in a
+ * FIFO queue (Sec. 4.2 Task Pool); whenever one of the server's slots is free
+ * the worker batches the oldest request's (layer, mode) group, admitting
+ * requests while the slot's output memory and max_batch allow, and launches
+ * the batch on the slot's own stream (a captured CUDA graph per slot and
+ * group when use_graphs is set).  Batches in different slots overlap on the
+ * device.  Completed tiles are handed out by hv_server_poll (Sec. 4.2 Result
+ * Pool, without expiry). */
 typedef struct hv_server_opts {
-    uint32_t max_batch;        /* tiles per launch (0 = 256) */
-    uint32_t queue_capacity;   /* pending requests before HV_EBUSY (0 = 65536) */
-    uint64_t scratch_bytes;    /* device bytes for tiles in flight (0 = 1 GiB) */
-    uint32_t index_kind;       /* HV_INDEX_* used for layers that have it */
-    uint32_t use_graphs;       /* capture launches into CUDA graphs */
+    uint32_t max_batch;        /* tiles per batch (0 = 64, at most 4096) */
+    uint32_t queue_capacity;   /* queued requests before HV_EBUSY (0 = 65536) */
+    uint64_t scratch_bytes;    /* device (and pinned host) bytes for slots: each
+                                  slot holds max_batch RGBA tiles; the number of
+                                  slots is scratch_bytes / slot size, 1..64
+                                  (0 = 1 GiB) */
+    uint32_t index_kind;       /* HV_INDEX_LEARNED to use learned indexes where
+                                  built; else the R-tree */
+    uint32_t use_graphs;       /* launch batches as captured CUDA graphs */
     hv_style style;
 } hv_server_opts;
 
 typedef struct hv_done {
     uint64_t tag;              /* the tag given to hv_server_submit */
     int32_t status;            /* HV_OK or an error code */
-    uint32_t bytes;            /* tile bytes written to `data` */
-    const uint8_t* data;       /* host pointer, valid until the next poll */
-    double t_submit_us, t_start_us, t_done_us;  /* host clock, microseconds */
+    uint32_t bytes;            /* tile bytes at `data` */
+    const uint8_t* data;       /* pinned host memory, valid until the next poll */
+    double t_submit_us, t_start_us, t_done_us;  /* steady host clock, microseconds */
 } hv_done;
 
+/* Start a server over n_layers built layers of `ctx`; a request's `layer`
+ * field indexes this array and its `mode` field selects the output. */
 int hv_server_start(hv_ctx* ctx, hv_layer* const* layers, uint32_t n_layers,
                     const hv_server_opts* opts, hv_server** out);
+/* Queue one request (checked as in hv_render_tiles): HV_EBUSY when the queue
+ * is full, HV_ESTATE once the server is stopping.  Thread-safe. */
 int hv_server_submit(hv_server* srv, const hv_tile_req* req, uint64_t tag);
+/* Hand out up to `max` completed requests; the data of the previous poll's
+ * results is released by this call. */
 int hv_server_poll(hv_server* srv, hv_done* out, uint32_t max, uint32_t* n_out);
+/* Finish queued and in-flight work, drop unpolled results and free the server
+ * (HV_ETIMEOUT if batches are still in flight after 120 s). */
 int hv_server_stop(hv_server* srv);
+/* Open-loop load: submit reqs[i] at arrival_us[i] microseconds after the call
+ * (as the queue allows), poll until all complete, and write each request's
+ * latency (completion - scheduled arrival, microseconds) to latency_us[i] and
+ * the total time to *wall_us.  Meant for measurement; do not poll
+ * concurrently. */
+int hv_server_replay(hv_server* srv, const hv_tile_req* reqs, const double* arrival_us, uint64_t n,
+                     double* latency_us, double* wall_us);
+/* Counters: batches launched, tiles launched, graph launches, slots. */
+int hv_server_stats(hv_server* srv, uint64_t* batches, uint64_t* tiles, uint64_t* graph_launches,
+                    uint32_t* slots);
 
 #ifdef __cplusplus
 }

@@ -170,6 +170,9 @@ int grow(Ctx* c, void** buf, uint64_t* cap, uint64_t need) {
 }
 
 }  // namespace
+
+void free_layer_public(Layer* L) { free_layer(L); }
+
 }  // namespace hv
 
 using namespace hv;

@@ -78,6 +78,7 @@ struct LearnedView {
     int64_t eps_linear = 0;             // ... of the linear pieces alone
     int64_t eps_mlp = 0;                // ... with the MLP residual
     double mean_err = 0;
+    double mean_window = 0;             // mean per-piece bound (search window)
     int32_t halo = 0;                   // max half-extent of indexed objects
     uint64_t n_obj = 0;
     // objects whose extent exceeds `halo` are also kept in a small side
@@ -140,7 +141,7 @@ struct RenderLog {
 };
 int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int index_kind,
                   const hv_style* style, uint8_t* d_out, cudaStream_t stream,
-                  const RenderLog* log = nullptr);
+                  const RenderLog* log = nullptr, const uint32_t* n_dev = nullptr);
 uint32_t render_launch_count(Layer* L, int index_kind);
 
 }  // namespace hv

@@ -17,7 +17,6 @@ int build_side_tree(Ctx* c, int4* objs, uint32_t* ids, uint64_t n, Tree* t, int4
 
 namespace {
 
-constexpr uint32_t kDefaultSegments = 0;   // 0 = choose P = 512 keys per piece
 constexpr int kDefaultHidden = kLearnH;
 constexpr int kDefaultSteps = 300;
 constexpr int kBatch = 1 << 16;
@@ -234,11 +233,17 @@ __global__ void k_eps(LModel m, uint32_t* eps, unsigned long long* sum_err) {
     if ((threadIdx.x & 31) == 0) atomicAdd(sum_err, s);
 }
 
-__global__ void k_max_u32(const uint32_t* a, uint32_t n, uint32_t* out) {
+// max and sum of the per-piece bounds (out[0] = max, out[1] = sum)
+__global__ void k_max_u32(const uint32_t* a, uint32_t n, unsigned long long* out) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t v = i < n ? a[i] : 0u;
-    v = __reduce_max_sync(kFull, v);
-    if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+    uint32_t mx = __reduce_max_sync(kFull, v);
+    unsigned long long sm = v;
+    for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(kFull, sm, o);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, (unsigned long long)mx);
+        atomicAdd(out + 1, sm);
+    }
 }
 
 // Half-extent of each object box (ceil of half the larger side) and a
@@ -325,21 +330,24 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
     // error of the linear pieces alone
     unsigned long long* scratch;
     HV_TRY(dev_alloc(c, (void**)&scratch, 64));
-    auto measure = [&](const LModel& mm, uint32_t* max_eps, double* mean) -> int {
+    // max bound, mean |error|, and the sum of per-piece bounds (the average
+    // search window, what a lookup pays)
+    auto measure = [&](const LModel& mm, uint32_t* max_eps, double* mean, double* sum_eps) -> int {
         cudaMemset(eps, 0, (uint64_t)n_seg * 4);
         cudaMemset(scratch, 0, 64);
         k_eps<<<blocks_for(n, 256), 256>>>(mm, eps, scratch);
-        k_max_u32<<<blocks_for(n_seg, 256), 256>>>(eps, n_seg, (uint32_t*)(scratch + 1));
-        unsigned long long h[2];
-        cudaError_t e = cudaMemcpy(h, scratch, 16, cudaMemcpyDeviceToHost);
+        k_max_u32<<<blocks_for(n_seg, 256), 256>>>(eps, n_seg, scratch + 1);
+        unsigned long long h[3];
+        cudaError_t e = cudaMemcpy(h, scratch, 24, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) { set_error("learned error pass: %s", cudaGetErrorString(e)); return HV_ECUDA; }
         *mean = (double)h[0] / (double)n;
         *max_eps = (uint32_t)h[1];
+        *sum_eps = (double)h[2];
         return HV_OK;
     };
     uint32_t eps_lin = 0, eps_mlp = 0;
-    double mean_lin = 0, mean_mlp = 0;
-    int rc = measure(m, &eps_lin, &mean_lin);
+    double mean_lin = 0, mean_mlp = 0, sum_lin = 0, sum_mlp = 0;
+    int rc = measure(m, &eps_lin, &mean_lin, &sum_lin);
     if (rc != HV_OK) { dev_free(c, scratch, 64); return rc; }
     // MLP residual, trained on the device
     cudaEvent_t t0, t1;
@@ -375,9 +383,11 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
         mm.hidden = H;
         mm.w = wb;
         mm.emb = embb;
-        rc = measure(mm, &eps_mlp, &mean_mlp);
+        rc = measure(mm, &eps_mlp, &mean_mlp, &sum_mlp);
         if (rc != HV_OK) { dev_free(c, scratch, 64); return rc; }
-        use_mlp = eps_mlp < eps_lin;
+        // keep the MLP when it narrows the average search window without
+        // widening the worst one by more than a quarter
+        use_mlp = sum_mlp < sum_lin && (double)eps_mlp <= 1.25 * (double)eps_lin;
         if (use_mlp) m = mm;
     }
     cudaEventRecord(t1);
@@ -388,7 +398,7 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
     cudaEventDestroy(t1);
     L->train_ms += ms;
     if (!use_mlp) {
-        rc = measure(m, &eps_lin, &mean_lin);  // restore the linear bounds
+        rc = measure(m, &eps_lin, &mean_lin, &sum_lin);  // restore the linear bounds
         if (rc != HV_OK) { dev_free(c, scratch, 64); return rc; }
     }
     dev_free(c, scratch, 64);
@@ -407,6 +417,7 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
     v.eps_linear = eps_lin;
     v.eps_mlp = eps_mlp;
     v.mean_err = use_mlp ? mean_mlp : mean_lin;
+    v.mean_window = (use_mlp ? sum_mlp : sum_lin) / (double)n_seg;
     *err_out = v.eps;
     // halo and side tree for objects with extent
     if (boxes_or_segs) {

@@ -51,6 +51,7 @@ struct TreeArg {
 struct Params {
     const hv_tile_req* reqs;
     uint32_t n;
+    const uint32_t* n_dev;      // if set, the batch size is min(*n_dev, n) (graph launches)
     int mode;
     int kind;
     uchar4 line;
@@ -130,8 +131,6 @@ struct Lane {
     int L;                 // warp-uniform: log2 of the pixel size
 };
 
-__device__ __forceinline__ int32_t sample_x(const Lane& s, int k) { return s.cx + ((k & 1) ? s.off : -s.off); }
-__device__ __forceinline__ int32_t sample_y(const Lane& s, int k) { return s.cy + ((k & 2) ? s.off : -s.off); }
 
 // Fold per-sample coverage masks (bit l: lane l's sample k was covered) into
 // the warp's undecided state.
@@ -432,96 +431,96 @@ __device__ __forceinline__ void set_levels(Smem& sm, int slot, const TreeArg& t,
         if (tid == l) sm.lvl_base[slot][l] = (l >= 1 && l <= t.top) ? t.nodes + t.level_off[l] * 128 : nullptr;
 }
 
-// Visit the R-tree subtrees that span sorted positions [lo, hi): the leaf
-// range is split into maximal aligned subtrees, whose boxes (stored in their
-// parent nodes) are tested before each visit.
-template <class V>
-__device__ void visit_range(const Params& p, Smem& sm, const Src& src, int top, uint64_t lo, uint64_t hi, Lane& s,
-                            int lane, int warp) {
-    uint64_t a = lo >> 5, b = (hi - 1) >> 5;
-    while (a <= b && s.U) {
-        int l = 0;
-        while (l + 1 < top && (a & ((1ull << (5 * (l + 1))) - 1)) == 0 && a + (1ull << (5 * (l + 1))) - 1 <= b) l++;
-        const int32_t* par = src.lvl[l + 1] + (a >> (5 * (l + 1))) * 128;
-        int c = (int)((a >> (5 * l)) & 31);
-        int32_t x0 = __ldg(par + c), y0 = __ldg(par + 32 + c), x1 = __ldg(par + 64 + c), y1 = __ldg(par + 96 + c);
-        if (reaches(s, V::kFill, rect_lanes(s, x0, y0, x1, y1), x0, y0, x1, y1)) {
-            if (l == 0)
-                V::visit(p, src, (uint32_t)a, s, lane);
-            else
-                descend<V>(p, sm, src, l, (uint32_t)(a >> (5 * l)), s, lane, warp);
-        }
-        a += 1ull << (5 * l);
-    }
-}
-
-// Learned candidate lookup for one block: cover the reach of the block's
-// undecided samples, widened by the halo of object extents, with at most 32
-// aligned Hilbert cells (the cells' key ranges are contiguous runs of the
-// sorted order); find each cell's position range through the model; visit
-// the R-tree subtrees spanning those positions; then search the side tree of
-// objects longer than the halo.
-template <class V>
-__device__ void learned_block(const Params& p, Smem& sm, const Src& src, const Src& side, int top, int side_top,
-                              const LModel& m, int32_t halo, Lane& s, int lane, int warp) {
-    int32_t ux0 = kEmptyLo, uy0 = kEmptyLo, ux1 = kEmptyHi, uy1 = kEmptyHi;
-    if (s.und) {
-        ux0 = s.cx - s.off; ux1 = s.cx + s.off;
-        uy0 = s.cy - s.off; uy1 = s.cy + s.off;
-    }
-    ux0 = __reduce_min_sync(kFull, ux0);
-    uy0 = __reduce_min_sync(kFull, uy0);
-    ux1 = __reduce_max_sync(kFull, ux1);
-    uy1 = __reduce_max_sync(kFull, uy1);
-    const int64_t e = (int64_t)(s.ext - s.off) + halo;
+// Learned cull (replaces the breadth-first R-tree cull): cover the strip's
+// box, widened by the halo of object extents, with at most 256 aligned
+// Hilbert cells (one per thread; a cell's keys are a contiguous run of the
+// sorted order), find each cell's position range through the learned model,
+// and turn the ranges into R-tree subtrees at the finest level whose entries
+// fit the frontier.  Every object whose centre lies in the box is under one of
+// the entries; the blocks then proceed exactly as after the R-tree cull.
+__device__ void learned_cull(const Params& p, const TreeArg& t, const LModel& m, int32_t halo, Smem& sm,
+                             int32_t bx0, int32_t by0, int32_t bx1, int32_t by1, int tid) {
+    __shared__ unsigned long long cnt[kMaxLevels + 1];
     const int64_t lo_g = -(int64_t)kGridHalf, hi_g = (int64_t)kGridHalf - 1;
-    int64_t qx0 = max((int64_t)ux0 - e, lo_g), qx1 = min((int64_t)ux1 + e, hi_g);
-    int64_t qy0 = max((int64_t)uy0 - e, lo_g), qy1 = min((int64_t)uy1 + e, hi_g);
-    if (m.n > 0 && qx0 <= qx1 && qy0 <= qy1) {
-        const int64_t W = qx1 - qx0 + 1, Hh = qy1 - qy0 + 1;
-        int k = 0;
-        while (k < 31 && (((int64_t)7 << k) < W || ((int64_t)3 << k) < Hh)) k++;
-        const int64_t gx0 = (qx0 + kGridHalf) >> k, gx1 = (qx1 + kGridHalf) >> k;
-        const int64_t gy0 = (qy0 + kGridHalf) >> k, gy1 = (qy1 + kGridHalf) >> k;
-        const int nx = (int)(gx1 - gx0 + 1), ny = (int)(gy1 - gy0 + 1);
-        int32_t cx0 = 0, cy0 = 0, cx1 = 0, cy1 = 0;
-        bool active = false;
-        uint64_t plo = 0, phi = 0;
-        if (lane < nx * ny) {
-            int64_t gx = gx0 + lane % nx, gy = gy0 + lane / nx;
-            int64_t x0 = (gx << k) - kGridHalf, y0 = (gy << k) - kGridHalf;
-            int64_t x1 = x0 + ((int64_t)1 << k) - 1, y1 = y0 + ((int64_t)1 << k) - 1;
-            // objects whose centre lies in the cell lie within the cell +- halo
-            cx0 = (int32_t)max(x0 - halo, lo_g); cy0 = (int32_t)max(y0 - halo, lo_g);
-            cx1 = (int32_t)min(x1 + halo, hi_g); cy1 = (int32_t)min(y1 + halo, hi_g);
-            active = reaches(s, V::kFill, rect_lanes(s, cx0, cy0, cx1, cy1), cx0, cy0, cx1, cy1);
-            if (active) {
-                uint64_t span = (k >= 31) ? (1ull << 62) : (1ull << (2 * k));
-                uint64_t klo = (k >= 31) ? 0ull : (hilbert_key((int32_t)x0, (int32_t)y0) & ~(span - 1));
-                bool fb;
-                plo = learn_lower_bound(m, klo, &fb);
-                phi = learn_lower_bound(m, klo + span, &fb);
+    const int64_t x0 = max((int64_t)bx0 - halo, lo_g), x1 = min((int64_t)bx1 + halo, hi_g);
+    const int64_t y0 = max((int64_t)by0 - halo, lo_g), y1 = min((int64_t)by1 + halo, hi_g);
+    if (tid <= kMaxLevels) cnt[tid] = 0;
+    if (tid == 0) {
+        sm.f_buf = 0;
+        sm.f_count = 0;
+        sm.f_level = 0;
+        sm.next_count = 0;
+    }
+    __syncthreads();
+    if (t.top == 0 || m.n == 0 || x0 > x1 || y0 > y1) return;
+    int k = 0;
+    while (k < 31) {
+        int64_t nx = ((x1 + kGridHalf) >> k) - ((x0 + kGridHalf) >> k) + 1;
+        int64_t ny = ((y1 + kGridHalf) >> k) - ((y0 + kGridHalf) >> k) + 1;
+        if (nx * ny <= kThreads) break;
+        k++;
+    }
+    const int64_t gx0 = (x0 + kGridHalf) >> k, gy0 = (y0 + kGridHalf) >> k;
+    const int nx = (int)(((x1 + kGridHalf) >> k) - gx0 + 1), ny = (int)(((y1 + kGridHalf) >> k) - gy0 + 1);
+    uint64_t a = 1, b = 0;   // leaf range of this thread's cell (empty)
+    if (tid < nx * ny) {
+        int64_t cx = ((gx0 + tid % nx) << k) - kGridHalf, cy = ((gy0 + tid / nx) << k) - kGridHalf;
+        uint64_t span = (k >= 31) ? (1ull << 62) : (1ull << (2 * k));
+        uint64_t klo = (k >= 31) ? 0ull : (hilbert_key((int32_t)cx, (int32_t)cy) & ~(span - 1));
+        bool fb;
+        uint64_t plo = learn_lower_bound(m, klo, &fb);
+        uint64_t phi = learn_lower_bound(m, klo + span, &fb);
+        if (phi > plo) {
+            a = plo >> 5;
+            b = (phi - 1) >> 5;
+        }
+    }
+    // entries per level: the leaves [a, b] span (b >> 5l) - (a >> 5l) + 1 subtrees of level l
+    for (int l = 0; l < t.top; l++)
+        if (a <= b) atomicAdd(&cnt[l], (unsigned long long)((b >> (5 * l)) - (a >> (5 * l)) + 1));
+    __syncthreads();
+    int lvl = t.top;   // no level fits: fall back to the root alone
+    for (int l = 0; l < t.top; l++)
+        if (cnt[l] <= (unsigned long long)kFCap) { lvl = l; break; }
+    if (lvl == t.top) {
+        if (tid == 0) {
+            sm.fid[0][0] = 0;
+            sm.fbox[0][0] = t.root_box;
+            sm.f_count = 1;
+            sm.f_level = t.top;
+        }
+        __syncthreads();
+        return;
+    }
+    if (a <= b) {
+        uint64_t e0 = a >> (5 * lvl), e1 = b >> (5 * lvl);
+        const int32_t* par = sm.lvl_base[0][lvl + 1];
+        for (uint64_t e = e0; e <= e1; e++) {
+            const int32_t* nd = par + (e >> 5) * 128;
+            int c = (int)(e & 31);
+            int4 bb = make_int4(__ldg(nd + c), __ldg(nd + 32 + c), __ldg(nd + 64 + c), __ldg(nd + 96 + c));
+            if (bb.x <= bx1 && bb.z >= bx0 && bb.y <= by1 && bb.w >= by0) {
+                int slot = atomicAdd(&sm.next_count, 1);
+                if (slot < kFCap) {
+                    sm.fid[0][slot] = (uint32_t)e;
+                    sm.fbox[0][slot] = bb;
+                }
             }
         }
-        uint32_t cm = __ballot_sync(kFull, active && phi > plo);
-        while (cm && s.U) {
-            int c = __ffs(cm) - 1;
-            cm &= cm - 1;
-            uint64_t a = __shfl_sync(kFull, plo, c), b = __shfl_sync(kFull, phi, c);
-            visit_range<V>(p, sm, src, top, a, b, s, lane, warp);
-            cm &= __ballot_sync(kFull, ((cm >> lane) & 1u) &&
-                                           reaches(s, V::kFill, rect_lanes(s, cx0, cy0, cx1, cy1), cx0, cy0, cx1, cy1));
-        }
     }
-    if (s.U && side_top > 0) descend<V>(p, sm, side, side_top, 0, s, lane, warp);
+    __syncthreads();
+    if (tid == 0) {
+        sm.f_count = min(sm.next_count, kFCap);
+        sm.f_level = lvl;
+    }
+    __syncthreads();
 }
 
 // Process every pixel block of the strip: against the culled frontier (R-tree)
 // or through the learned lookup.
 template <class V>
-__device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src& side, int top, int side_top,
-                            const LModel* m, int32_t halo, int32_t X0, int32_t Y0, int strip, int z, int32_t R,
-                            bool mask_mode, int tid) {
+__device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src& side, int side_top, int32_t X0,
+                            int32_t Y0, int strip, int z, int32_t R, bool mask_mode, int tid) {
     int lane = tid & 31, warp = tid >> 5;
     const int L = 23 - z;
     const int32_t ps = 1 << L;
@@ -555,9 +554,7 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         s.U = kFull;
         for (int k = 0; k < 4; k++) s.Uk[k] = k < s.nk ? kFull : 0u;
         uint32_t und0 = s.und;
-        if (m != nullptr) {
-            learned_block<V>(p, sm, src, side, top, side_top, *m, halo, s, lane, warp);
-        } else {
+        {
             for (int c0 = 0; c0 < f_count && s.U; c0 += 32) {
                 int e = c0 + lane;
                 uint32_t cm = 0;
@@ -581,6 +578,8 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                                                    reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
                 }
             }
+            // objects longer than the learned index's halo live in a side tree
+            if (side_top > 0 && s.U) descend<V>(p, sm, side, side_top, 0, s, lane, warp);
         }
         uint32_t covered = und0 & ~s.und;
         uint8_t r = sm.res[jl * kTile + i];
@@ -596,8 +595,8 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
 }
 
 // One stage (Algorithm 1 over points / segments / edges, or Algorithm 2 over
-// polygon boxes) for the strip: cull (R-tree) or check the layer box
-// (learned), then every block.
+// polygon boxes) for the strip: cull through the R-tree or the learned
+// index, then every block.
 template <class V>
 __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* obj, const uint32_t* ids,
                       const TreeArg& st, const void* sobj, const uint32_t* sids, const LModel* m, int32_t halo,
@@ -607,19 +606,16 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
     set_levels(sm, 1, st, tid);
     if (tid == 0) sm.next_block = 0;
     __syncthreads();
-    bool any;
-    if (m == nullptr) {
+    if (m == nullptr)
         cull(p, t, V::kFill, sm, bx0, by0, bx1, by1, tid);
-        any = sm.f_count > 0;
-    } else {
-        int4 rb = t.root_box, sb = st.root_box;
-        any = (t.top > 0 && rb.x <= bx1 && rb.z >= bx0 && rb.y <= by1 && rb.w >= by0) ||
-              (st.top > 0 && sb.x <= bx1 && sb.z >= bx0 && sb.y <= by1 && sb.w >= by0);
-    }
-    if (any) {
+    else
+        learned_cull(p, t, *m, halo, sm, bx0, by0, bx1, by1, tid);
+    int4 sb = st.root_box;
+    bool side_hit = st.top > 0 && sb.x <= bx1 && sb.z >= bx0 && sb.y <= by1 && sb.w >= by0;
+    if (sm.f_count > 0 || side_hit) {
         Src src{obj, ids, t.n_obj, t.nodes, sm.lvl_base[0]};
         Src side{sobj, sids, st.n_obj, st.nodes, sm.lvl_base[1]};
-        blocks_pass<V>(p, sm, src, side, t.top, st.top, m, halo, X0, Y0, strip, z, R, mask_mode, tid);
+        blocks_pass<V>(p, sm, src, side, side_hit ? st.top : 0, X0, Y0, strip, z, R, mask_mode, tid);
     }
     __syncthreads();
 }
@@ -629,7 +625,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
     const int tid = threadIdx.x;
     const uint32_t tile = blockIdx.x / kStrips;
     const int strip = blockIdx.x % kStrips;
-    if (tile >= p.n) return;
+    const uint32_t n = p.n_dev ? min(*p.n_dev, p.n) : p.n;
+    if (tile >= n) return;
     hv_tile_req q = p.reqs[tile];
     bool ok = q.z <= 19 && q.x < (1u << q.z) && q.y < (1u << q.z) && q.r16 >= 1 && q.r16 <= 1024;
     for (int k = tid; k < kStripRows * kTile / 4; k += kThreads) ((uint32_t*)sm.res)[k] = 0u;
@@ -735,13 +732,15 @@ LModel learned_model(const LearnedView& v);
 uint32_t render_launch_count(Layer*, int) { return 1; }
 
 int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int index_kind,
-                  const hv_style* style, uint8_t* d_out, cudaStream_t stream, const RenderLog* log) {
+                  const hv_style* style, uint8_t* d_out, cudaStream_t stream, const RenderLog* log,
+                  const uint32_t* n_dev) {
     (void)index_kind;
     if (n == 0) return HV_OK;
     Params p;
     memset(&p, 0, sizeof(p));
     p.reqs = d_reqs;
     p.n = n;
+    p.n_dev = n_dev;
     p.mode = mode;
     p.kind = L->kind;
     if (style) {

@@ -100,6 +100,8 @@ SIGNATURES = {
     "hv_server_submit": [P, P, U64],
     "hv_server_poll": [P, ctypes.POINTER(hv_done), U32, ctypes.POINTER(U32)],
     "hv_server_stop": [P],
+    "hv_server_replay": [P, P, P, U64, P, ctypes.POINTER(ctypes.c_double)],
+    "hv_server_stats": [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U32)],
 }
 
 
@@ -318,6 +320,31 @@ def hv_server_poll(srv, buf):
 
 def hv_server_stop(srv):
     _check(lib().hv_server_stop(srv))
+
+
+def hv_server_replay(srv, reqs, arrival_us):
+    """Open-loop replay; returns (latency_us array, wall_us)."""
+    arr = np.ascontiguousarray(arrival_us, dtype=np.float64)
+    lat = np.zeros(len(reqs), dtype=np.float64)
+    wall = ctypes.c_double()
+    _check(lib().hv_server_replay(srv, ptr(reqs), ptr(arr), len(reqs), ptr(lat), ctypes.byref(wall)))
+    return lat, wall.value
+
+
+def hv_server_stats(srv):
+    b, t, g, s = U64(), U64(), U64(), U32()
+    _check(lib().hv_server_stats(srv, ctypes.byref(b), ctypes.byref(t), ctypes.byref(g), ctypes.byref(s)))
+    return {"batches": b.value, "tiles": t.value, "graph_launches": g.value, "slots": s.value}
+
+
+def make_server_opts(max_batch=64, queue_capacity=0, scratch_bytes=0, index_kind=HV_INDEX_RTREE,
+                     use_graphs=1, style=None):
+    o = hv_server_opts()
+    o.max_batch, o.queue_capacity, o.scratch_bytes = max_batch, queue_capacity, scratch_bytes
+    o.index_kind, o.use_graphs = index_kind, use_graphs
+    if style is not None:
+        o.style = style
+    return o
 
 
 # ---- convenience: render host arrays into a numpy result --------------------

@@ -298,3 +298,59 @@ def config4(n_polys=2_000_000, n_tiles=10_000):
     xy, ro, po = star_polygons(n_polys, seed=4)
     cen = polygon_centres(xy, ro, po)
     return xy, ro, po, density_tiles(cen, n_tiles, 4, 14, 8, seed=104)
+
+
+def pan_zoom_trace(anchors, n, seed, n_sessions=256, z_start=10, z_min=2, z_max=18, zipf_s=1.1,
+                   r16_range=(16, 48), p_pan=0.7):
+    """Tile requests from seeded pan / zoom browsing sessions (the request
+    stream of HiVision Exp. 3, shaped as interactive map use).
+
+    ``anchors`` holds one (m, 2) anchor array per layer.  Each session picks a
+    layer uniformly and a start tile at zoom ``z_start`` drawn Zipf(s) over the
+    layer's tiles ranked by anchor count; each step pans to one of the 8
+    neighbours (probability p_pan) or zooms in / out by one level (clamped to
+    [z_min, z_max]).  Sessions are interleaved uniformly at random.  r16 is
+    uniform in r16_range.  Returns an (n, 5) array [z, x, y, r16, layer]."""
+    rng = rng_for(seed)
+    starts = []
+    for a in anchors:
+        t = tile_of(a, z_start)
+        key = (t[:, 0] << 32) | t[:, 1]
+        uk, cnt = np.unique(key, return_counts=True)
+        order = np.argsort(-cnt, kind="stable")
+        ranked = uk[order]
+        w = 1.0 / np.arange(1, len(ranked) + 1) ** zipf_s
+        starts.append((ranked, w / w.sum()))
+    state = np.zeros((n_sessions, 4), dtype=np.int64)   # layer, z, x, y
+    for s in range(n_sessions):
+        layer = int(rng.integers(0, len(anchors)))
+        ranked, p = starts[layer]
+        k = ranked[rng.choice(len(ranked), p=p)]
+        state[s] = (layer, z_start, k >> 32, k & 0xFFFFFFFF)
+    out = np.zeros((n, 5), dtype=np.int64)
+    who = rng.integers(0, n_sessions, size=n)
+    u = rng.random(n)
+    nb = rng.integers(0, 8, size=n)
+    kid = rng.integers(0, 4, size=n)
+    r16 = rng.integers(r16_range[0], r16_range[1] + 1, size=n)
+    moves = np.array([(-1, -1), (0, -1), (1, -1), (-1, 0), (1, 0), (-1, 1), (0, 1), (1, 1)])
+    for i in range(n):
+        layer, z, x, y = state[who[i]]
+        if u[i] < p_pan:
+            dx, dy = moves[nb[i]]
+            m = (1 << z) - 1
+            x, y = min(max(x + dx, 0), m), min(max(y + dy, 0), m)
+        elif u[i] < p_pan + (1 - p_pan) / 2:
+            if z < z_max:
+                z, x, y = z + 1, 2 * x + (kid[i] & 1), 2 * y + (kid[i] >> 1)
+        elif z > z_min:
+            z, x, y = z - 1, x >> 1, y >> 1
+        state[who[i]] = (layer, z, x, y)
+        out[i] = (z, x, y, r16[i], layer)
+    return out
+
+
+def poisson_arrivals(n, rate, seed):
+    """Arrival times (microseconds) of an open-loop Poisson stream."""
+    rng = rng_for(seed)
+    return np.cumsum(rng.exponential(1e6 / rate, size=n))
