@@ -150,27 +150,31 @@ class Layer:
         n = args.points or w["n_objects"]
         r16 = args.r16 or w["r16"]
         z0, z1 = w["zoom"]
+        # every rank renders its own args.tiles tiles: shard `rank` of a batch
+        # of args.tiles * world requests (weak scaling over replicas)
+        world = dist_env()[1]
         if cfg == 2:
             self.kind = "points"
             self.xy = gen.gmm_points(n, seed=2, k=64)
-            self.reqs = gen.density_tiles(self.xy, args.tiles, z0, z1, r16, seed=102 + rank)
+            all_reqs = gen.density_tiles(self.xy, args.tiles * world, z0, z1, r16, seed=102)
             self.obj_bytes = 8
         elif cfg == 3:
             self.kind = "lines"
             n_lines = max(1, n // 10)
             self.xy, self.off = gen.walk_lines(n_lines, n, seed=3)
             mids = gen.segment_midpoints(self.xy, self.off, max_n=4 * args.tiles, seed=103)
-            self.reqs = gen.density_tiles(mids, args.tiles, z0, z1, r16, seed=203 + rank)
+            all_reqs = gen.density_tiles(mids, args.tiles * world, z0, z1, r16, seed=203)
             self.obj_bytes = 16
         else:
             self.kind = "polygons"
             self.xy, self.ro, self.po = gen.star_polygons(n, seed=4)
             cen = gen.polygon_centres(self.xy, self.ro, self.po)
-            self.reqs = gen.density_tiles(cen, args.tiles, z0, z1, r16, seed=104 + rank)
+            all_reqs = gen.density_tiles(cen, args.tiles * world, z0, z1, r16, seed=104)
             self.obj_bytes = 16
             ro = np.asarray(self.ro, dtype=np.int64)
             po = np.asarray(self.po, dtype=np.int64)
             self.poly_edges = ro[po[1:]] - ro[po[:-1]]
+        self.reqs = gen.shard(all_reqs, rank, world)
         self.n_objects = n
 
     def load(self, hv, ctx):

@@ -369,24 +369,23 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
     }
 }
 
-// Breadth-first cull of a tree against a box into the shared frontier.
-__device__ void cull(const Params& p, const TreeArg& t, bool fill, Smem& sm, int32_t x0, int32_t y0,
-                     int32_t x1, int32_t y1, int tid) {
+// Level bases of a tree into shared memory slot `slot` (0: the tree being
+// traversed, 1: its side tree).
+__device__ __forceinline__ void set_levels(Smem& sm, int slot, const TreeArg& t, int tid) {
+#pragma unroll
+    for (int l = 0; l <= kMaxLevels; l++)
+        if (tid == l) sm.lvl_base[slot][l] = (l >= 1 && l <= t.top) ? t.nodes + t.level_off[l] * 128 : nullptr;
+}
+
+// Refine the shared frontier breadth first: replace every entry by its
+// children that meet the box, one level at a time, while the next level fits
+// (the deepest level that fits is kept).
+__device__ void refine(const Params& p, const TreeArg& t, bool fill, Smem& sm, int32_t x0, int32_t y0,
+                       int32_t x1, int32_t y1, int tid) {
     int lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        sm.f_buf = 0;
-        sm.f_level = t.top;
-        sm.f_count = 0;
-        if (t.top > 0 && t.root_box.x <= x1 && t.root_box.z >= x0 && t.root_box.y <= y1 &&
-            t.root_box.w >= y0) {
-            sm.fid[0][0] = 0;
-            sm.fbox[0][0] = t.root_box;
-            sm.f_count = 1;
-        }
-    }
-    __syncthreads();
     while (sm.f_level >= 1 && sm.f_count > 0) {
         int cur = sm.f_buf, lvl = sm.f_level, cnt = sm.f_count;
+        __syncthreads();
         if (tid == 0) sm.next_count = 0;
         __syncthreads();
         const int32_t* base = sm.lvl_base[0][lvl];
@@ -423,12 +422,23 @@ __device__ void cull(const Params& p, const TreeArg& t, bool fill, Smem& sm, int
     }
 }
 
-// Level bases of a tree into shared memory slot `slot` (0: the tree being
-// traversed, 1: its side tree).
-__device__ __forceinline__ void set_levels(Smem& sm, int slot, const TreeArg& t, int tid) {
-#pragma unroll
-    for (int l = 0; l <= kMaxLevels; l++)
-        if (tid == l) sm.lvl_base[slot][l] = (l >= 1 && l <= t.top) ? t.nodes + t.level_off[l] * 128 : nullptr;
+// Breadth-first cull of a tree against a box into the shared frontier,
+// starting from the root.
+__device__ void cull(const Params& p, const TreeArg& t, bool fill, Smem& sm, int32_t x0, int32_t y0,
+                     int32_t x1, int32_t y1, int tid) {
+    if (tid == 0) {
+        sm.f_buf = 0;
+        sm.f_level = t.top;
+        sm.f_count = 0;
+        if (t.top > 0 && t.root_box.x <= x1 && t.root_box.z >= x0 && t.root_box.y <= y1 &&
+            t.root_box.w >= y0) {
+            sm.fid[0][0] = 0;
+            sm.fbox[0][0] = t.root_box;
+            sm.f_count = 1;
+        }
+    }
+    __syncthreads();
+    refine(p, t, fill, sm, x0, y0, x1, y1, tid);
 }
 
 // Learned cull (replaces the breadth-first R-tree cull): cover the strip's
@@ -490,6 +500,7 @@ __device__ void learned_cull(const Params& p, const TreeArg& t, const LModel& m,
             sm.f_level = t.top;
         }
         __syncthreads();
+        refine(p, t, false, sm, bx0, by0, bx1, by1, tid);
         return;
     }
     if (a <= b) {
@@ -514,6 +525,7 @@ __device__ void learned_cull(const Params& p, const TreeArg& t, const LModel& m,
         sm.f_level = lvl;
     }
     __syncthreads();
+    refine(p, t, false, sm, bx0, by0, bx1, by1, tid);
 }
 
 // Process every pixel block of the strip: against the culled frontier (R-tree)

@@ -354,3 +354,12 @@ def poisson_arrivals(n, rate, seed):
     """Arrival times (microseconds) of an open-loop Poisson stream."""
     rng = rng_for(seed)
     return np.cumsum(rng.exponential(1e6 / rate, size=n))
+
+
+def shard(rows, rank, world):
+    """Contiguous shard `rank` of `world` of a request array (replica serving:
+    every rank holds the whole layer and renders its own share of tiles)."""
+    n = len(rows)
+    lo = (n * rank) // world
+    hi = (n * (rank + 1)) // world
+    return rows[lo:hi]
