@@ -93,6 +93,7 @@ SIGNATURES = {
     "hv_layer_load_file": [P, ctypes.c_char_p, ctypes.POINTER(P)],
     "hv_tile_bytes": [I32],
     "hv_render_tiles": [P, P, U32, I32, I32, P, P, U64, P],
+    "hv_render_tiles_static": [P, P, U32, I32, I32, P, P, U64, P],
     "hv_layer_take_status": [P, P, ctypes.POINTER(U32)],
     "hv_render_tiles_counted": [P, P, U32, I32, I32, P, P, U64, P, U64, P, P],
     "hv_render_launches": [P, I32, ctypes.POINTER(U32)],
@@ -283,6 +284,13 @@ def hv_render_tiles_counted(layer, reqs, n, mode, index_kind, style, out, out_by
                                          ctypes.byref(style) if style is not None else None, ptr(out),
                                          out_bytes, ptr(log), log_cap, ptr(log_count),
                                          stream_handle(stream)))
+
+
+def hv_render_tiles_static(layer, reqs, n, mode, index_kind, style, out, out_bytes, stream=None):
+    """Allocation-free rendering: `out` must be device memory (see the header)."""
+    _check(lib().hv_render_tiles_static(layer, ptr(reqs), n, mode, index_kind,
+                                        ctypes.byref(style) if style is not None else None, ptr(out),
+                                        out_bytes, stream_handle(stream)))
 
 
 def hv_layer_take_status(layer, stream=None):

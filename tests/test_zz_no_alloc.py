@@ -1,0 +1,50 @@
+"""The allocation-free entry point against the allocating one.
+
+hv_render_tiles_static serves callers that may not allocate device memory
+(for example inside a stream capture, or when another allocator owns the
+device): it stages requests in a fixed device array of the library instead
+of cudaMalloc'd scratch.  Its tiles must equal hv_render_tiles' exactly, call
+after call, although every call reuses the same staging array.
+"""
+import numpy as np
+import pytest
+
+from workloads import gen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2005_12489_gb300 import hv  # noqa: E402
+
+
+def test_static_entry_matches_allocating_entry():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    ctx = hv.hv_create(0)
+    try:
+        pts = gen.gmm_points(300_000, seed=91, k=16)
+        L = hv.hv_layer_load_points(ctx, pts)
+        hv.hv_layer_build_index(L, hv.HV_INDEX_RTREE)
+        style = hv.make_style((200, 30, 60), (20, 140, 250))
+        stream = torch.cuda.current_stream()
+        try:
+            # two calls in a row with different requests: the second must not
+            # see anything of the first in the shared staging array
+            for seed, n, mode in ((92, 300, hv.HV_MODE_RGBA), (93, 17, hv.HV_MODE_COVERAGE)):
+                reqs = hv.make_requests(gen.density_tiles(pts, n, 3, 15, [8, 32], seed=seed))
+                tb = hv.hv_tile_bytes(mode)
+                ref = torch.zeros((n, tb), dtype=torch.uint8, device="cuda")
+                hv.hv_render_tiles(L, reqs, n, mode, hv.HV_INDEX_RTREE, style, ref, ref.numel(), stream)
+                got = torch.full((n, tb), 0xAB, dtype=torch.uint8, device="cuda")
+                hv.hv_render_tiles_static(L, reqs, n, mode, hv.HV_INDEX_RTREE, style, got, got.numel(), stream)
+                stream.synchronize()
+                assert torch.equal(got, ref)
+            with pytest.raises(hv.HVError) as e:
+                big = hv.make_requests(np.tile([[3, 1, 1, 16]], (4097, 1)))
+                hv.hv_render_tiles_static(L, big, 4097, hv.HV_MODE_MASK, hv.HV_INDEX_RTREE, None, got,
+                                          got.numel(), stream)
+            assert e.value.status == hv.HV_EINVAL
+        finally:
+            hv.hv_layer_free(L)
+    finally:
+        hv.hv_destroy(ctx)
