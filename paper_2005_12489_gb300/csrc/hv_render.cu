@@ -454,6 +454,11 @@ __device__ void learned_cull(const Params& p, const TreeArg& t, const LModel& m,
     const int64_t lo_g = -(int64_t)kGridHalf, hi_g = (int64_t)kGridHalf - 1;
     const int64_t x0 = max((int64_t)bx0 - halo, lo_g), x1 = min((int64_t)bx1 + halo, hi_g);
     const int64_t y0 = max((int64_t)by0 - halo, lo_g), y1 = min((int64_t)by1 + halo, hi_g);
+    // neighbouring cells share subtrees: a hash set in the (idle) second
+    // frontier buffer keeps each entry once
+    uint32_t* seen = (uint32_t*)sm.fbox[1];
+    constexpr int kSeen = 1024;
+    for (int i = tid; i < kSeen; i += kThreads) seen[i] = 0u;
     if (tid <= kMaxLevels) cnt[tid] = 0;
     if (tid == 0) {
         sm.f_buf = 0;
@@ -511,6 +516,10 @@ __device__ void learned_cull(const Params& p, const TreeArg& t, const LModel& m,
             int c = (int)(e & 31);
             int4 bb = make_int4(__ldg(nd + c), __ldg(nd + 32 + c), __ldg(nd + 64 + c), __ldg(nd + 96 + c));
             if (bb.x <= bx1 && bb.z >= bx0 && bb.y <= by1 && bb.w >= by0) {
+                // at most kFCap distinct entries, so the set never fills
+                uint32_t key = (uint32_t)e + 1u, h = (key * 2654435761u) & (kSeen - 1), prev;
+                while ((prev = atomicCAS(&seen[h], 0u, key)) != 0u && prev != key) h = (h + 1) & (kSeen - 1);
+                if (prev == key) continue;
                 int slot = atomicAdd(&sm.next_count, 1);
                 if (slot < kFCap) {
                     sm.fid[0][slot] = (uint32_t)e;
