@@ -164,13 +164,13 @@ class Layer:
             self.xy, self.off = gen.walk_lines(n_lines, n, seed=3)
             mids = gen.segment_midpoints(self.xy, self.off, max_n=4 * args.tiles, seed=103)
             all_reqs = gen.density_tiles(mids, args.tiles * world, z0, z1, r16, seed=203)
-            self.obj_bytes = 16
+            self.obj_bytes = 32      # index record: segment + piece box
         else:
             self.kind = "polygons"
             self.xy, self.ro, self.po = gen.star_polygons(n, seed=4)
             cen = gen.polygon_centres(self.xy, self.ro, self.po)
             all_reqs = gen.density_tiles(cen, args.tiles * world, z0, z1, r16, seed=104)
-            self.obj_bytes = 16
+            self.obj_bytes = 32      # index record: edge + piece box
             ro = np.asarray(self.ro, dtype=np.int64)
             po = np.asarray(self.po, dtype=np.int64)
             self.poly_edges = ro[po[1:]] - ro[po[:-1]]
@@ -427,7 +427,8 @@ def run_gb300(args):
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                 "index_timed": args.index, "learned": learned, "latency": lat,
                 "wall_s_timed_region": wall, "step_ms": step_ms,
-                "index_build_ms": info.build_ms, "tree_levels": info.tree_levels}
+                "index_build_ms": info.build_ms, "tree_levels": info.tree_levels,
+                "index_records": info.index_records, "piece_extent": info.piece_extent}
         print(json.dumps(line), flush=True)
     hv.hv_layer_free(layer)
     hv.hv_destroy(ctx)

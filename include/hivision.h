@@ -134,7 +134,10 @@ typedef struct hv_layer_info {
     uint32_t learned_pieces;       /* piecewise-linear pieces */
     uint32_t learned_mlp;          /* 1 if the MLP residual is in use */
     int32_t learned_halo;          /* half-extent covered through centre keys */
-    int32_t reserved;
+    int32_t piece_extent;          /* segment layers: segments are indexed as
+                                      pieces of at most this extent */
+    uint64_t index_records;        /* records in the object R-tree (points, or
+                                      segment pieces) */
 } hv_layer_info;
 
 /* ---- context ------------------------------------------------------------ */
@@ -180,8 +183,9 @@ int hv_layer_build_index(hv_layer* layer, uint32_t kinds, const hv_build_opts* o
 
 int hv_layer_info_get(hv_layer* layer, hv_layer_info* out);
 
-/* Copy the sorted Hilbert keys of a built layer (which = 0: objects, 1:
- * polygon boxes) into `out` (device memory, n entries, n = objects / polygons). */
+/* Copy the sorted Hilbert keys of a built layer (which = 0: index records,
+ * 1: polygon boxes) into `out` (device memory, n entries, n = index_records /
+ * polygons of hv_layer_info). */
 int hv_layer_keys(hv_layer* layer, int which, uint64_t* out, uint64_t n);
 
 /* lower_bound of each query key in the sorted keys through the learned model

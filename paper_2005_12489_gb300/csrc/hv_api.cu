@@ -136,7 +136,7 @@ void free_layer(Layer* L) {
     if (L->keys) dev_free(c, L->keys, L->n_obj * 8);
     free_tree(c, &L->tree);
     if (L->kind == HV_LAYER_POLYGONS) {
-        dev_free(c, L->poly_edges, (L->n_obj ? L->n_obj : 1) * 16);
+        dev_free(c, L->poly_edges, (L->n_src ? L->n_src : 1) * 16);
         dev_free(c, L->poly_edge_off, (L->n_poly + 1) * 8);
         dev_free(c, L->mbr_obj, (L->n_poly ? L->n_poly : 1) * 16);
         if (L->mbr_ids) dev_free(c, L->mbr_ids, L->n_poly * 4);
@@ -235,6 +235,7 @@ int hv_layer_load_points(hv_ctx* ctx, const int32_t* xy, uint64_t n, hv_layer** 
     L->obj = d;
     L->obj_bytes = n * 8;
     L->n_obj = n;
+    L->n_src = n;
     return finish_layer(L, out);
 }
 
@@ -257,6 +258,7 @@ int hv_layer_load_linestrings(hv_ctx* ctx, const int32_t* xy, uint64_t n_vert, c
     L->obj = segs;
     L->obj_bytes = n_seg ? n_seg * 16 : 0;
     L->n_obj = n_seg;
+    L->n_src = n_seg;
     return finish_layer(L, out);
 }
 
@@ -315,8 +317,10 @@ int hv_layer_info_get(hv_layer* layer, hv_layer_info* out) {
     memset(out, 0, sizeof(*out));
     out->kind = L->kind;
     out->indexes = L->indexes;
-    out->n_objects = L->n_obj;
+    out->n_objects = L->n_src;
     out->n_polygons = L->n_poly;
+    out->index_records = L->n_obj;
+    out->piece_extent = L->piece_extent;
     if (L->tree.view.top) {
         out->mbr[0] = L->mbr.x; out->mbr[1] = L->mbr.y; out->mbr[2] = L->mbr.z; out->mbr[3] = L->mbr.w;
     }
@@ -337,7 +341,7 @@ int hv_layer_info_get(hv_layer* layer, hv_layer_info* out) {
     }
     uint64_t bytes = L->obj_bytes + (L->keys ? L->n_obj * 8 : 0) + L->tree.nodes_bytes;
     if (L->kind == HV_LAYER_POLYGONS)
-        bytes += L->n_obj * 16 + (L->n_poly + 1) * 8 + L->n_poly * (16 + 4 + 8) + L->mbr_tree.nodes_bytes;
+        bytes += L->n_src * 16 + (L->n_poly + 1) * 8 + L->n_poly * (16 + 4 + 8) + L->mbr_tree.nodes_bytes;
     for (auto& a : L->learned.allocs) bytes += a.second;
     for (auto& a : L->mbr_learned.allocs) bytes += a.second;
     out->device_bytes = bytes;

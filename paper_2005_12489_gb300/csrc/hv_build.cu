@@ -5,6 +5,7 @@
 // 32 to a leaf, and every inner node stores the 32 boxes of its children as
 // SoA int32 so one warp reads a node with four coalesced 128-byte loads.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 
 #include "hv_device.cuh"
 #include "hv_internal.h"
@@ -27,12 +28,17 @@ struct BoxObj {
     using T = int4;
     __device__ static int4 box(int4 b) { return b; }
 };
+struct PieceObj {
+    using T = Piece;
+    __device__ static int4 box(const Piece& p) { return p.box; }
+};
 
 template <class O>
 __global__ void k_keys(const typename O::T* obj, uint64_t n, uint64_t* keys, uint32_t* idx) {
     uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int4 b = O::box(obj[i]);
+    const typename O::T o = obj[i];
+    int4 b = O::box(o);
     uint64_t k;
     if (b.x > b.z) {
         k = (1ull << 62) - 1;  // empty box: sorts last, never intersects
@@ -61,7 +67,11 @@ __global__ void k_leaf_boxes(const typename O::T* obj, uint64_t n, uint64_t n_le
     int lane = threadIdx.x & 31;
     if (leaf >= n_leaf) return;
     uint64_t i = leaf * 32 + lane;
-    int4 b = i < n ? O::box(obj[i]) : make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
+    int4 b = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
+    if (i < n) {
+        const typename O::T o = obj[i];
+        b = O::box(o);
+    }
     b = warp_union(b);
     if (lane == 0) box[leaf] = b;
 }
@@ -246,7 +256,112 @@ __global__ void k_poly_boxes(const int4* edges, const uint64_t* ring_off, const 
     }
 }
 
+// ---- segment pieces ----------------------------------------------------------
+
+__device__ __forceinline__ int64_t seg_extent(int4 s) {
+    int64_t dx = (int64_t)s.z - s.x, dy = (int64_t)s.w - s.y;
+    dx = dx < 0 ? -dx : dx;
+    dy = dy < 0 ? -dy : dy;
+    return dx > dy ? dx : dy;
+}
+
+__global__ void k_extent_bits(const int4* segs, uint64_t n, unsigned long long* hist) {
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t e = seg_extent(segs[i]);
+    atomicAdd(hist + (64 - __clzll((unsigned long long)e)), 1ull);
+}
+
+constexpr uint32_t kMaxPieces = 4096;
+
+__global__ void k_widen(const uint32_t* a, uint64_t n, uint64_t* b) {
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+__global__ void k_piece_count(const int4* segs, uint64_t n, int shift, uint32_t* cnt) {
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t m = ((uint64_t)seg_extent(segs[i]) >> shift) + 1;
+    cnt[i] = (uint32_t)(m < kMaxPieces ? m : kMaxPieces);
+}
+
+__device__ __forceinline__ int64_t floordiv64(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+// Piece k of m covers the parameter interval [k/m, (k+1)/m]; along each axis
+// the segment moves monotonically, so the piece lies between its two end
+// positions, rounded outwards to the grid.
+__global__ void k_emit_pieces(const int4* segs, uint64_t n, const uint32_t* cnt, const uint64_t* off,
+                              Piece* out) {
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 s = segs[i];
+    int64_t m = cnt[i];
+    int64_t dx = (int64_t)s.z - s.x, dy = (int64_t)s.w - s.y;
+    uint64_t o = off[i];
+    for (int64_t k = 0; k < m; k++) {
+        int64_t xa = floordiv64(dx * k, m), xb = floordiv64(dx * (k + 1), m);
+        int64_t ya = floordiv64(dy * k, m), yb = floordiv64(dy * (k + 1), m);
+        // exact positions lie in [floor, floor + 1)
+        int64_t x0 = s.x + (xa < xb ? xa : xb), x1 = s.x + (xa > xb ? xa : xb) + 1;
+        int64_t y0 = s.y + (ya < yb ? ya : yb), y1 = s.y + (ya > yb ? ya : yb) + 1;
+        int4 b = make_int4((int32_t)max(x0, (int64_t)min(s.x, s.z)), (int32_t)max(y0, (int64_t)min(s.y, s.w)),
+                           (int32_t)min(x1, (int64_t)max(s.x, s.z)), (int32_t)min(y1, (int64_t)max(s.y, s.w)));
+        out[o + k] = Piece{s, b};
+    }
+}
+
 }  // namespace
+
+// Split n segments into pieces of extent at most 2^shift (the smallest power
+// of two, at least 2^12, for which the pieces number at most 4n).
+int make_pieces(Ctx* c, const int4* segs, uint64_t n, Piece** out, uint64_t* n_out, int32_t* extent) {
+    *out = nullptr;
+    *n_out = 0;
+    *extent = 0;
+    if (n == 0) return HV_OK;
+    Tmp tmp(c);
+    unsigned long long* hist;
+    HV_TRY(tmp.get((void**)&hist, 65 * 8));
+    HV_CUDA(cudaMemset(hist, 0, 65 * 8));
+    k_extent_bits<<<grid_for(n, 256), 256>>>(segs, n, hist);
+    unsigned long long h[65];
+    HV_CUDA(cudaMemcpy(h, hist, sizeof(h), cudaMemcpyDeviceToHost));
+    int shift = 12;
+    for (; shift < 31; shift++) {
+        // an extent of bit length b is < 2^b: at most (2^b >> shift) + 1 pieces
+        double total = 0;
+        for (int b = 0; b < 65; b++) total += (double)h[b] * (double)(((b >= 63 ? ~0ull : (1ull << b)) >> shift) + 1);
+        if (total <= 4.0 * (double)n) break;
+    }
+    uint32_t* cnt;
+    uint64_t *cnt64, *off;
+    HV_TRY(tmp.get((void**)&cnt, n * 4));
+    HV_TRY(tmp.get((void**)&cnt64, (n + 1) * 8));
+    HV_TRY(tmp.get((void**)&off, (n + 1) * 8));
+    k_piece_count<<<grid_for(n, 256), 256>>>(segs, n, shift, cnt);
+    // 64-bit exclusive prefix sum of the counts (entry n holds the total)
+    HV_CUDA(cudaMemset(cnt64, 0, (n + 1) * 8));
+    k_widen<<<grid_for(n, 256), 256>>>(cnt, n, cnt64);
+    size_t tb = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt64, off, (int64_t)(n + 1));
+    void* temp;
+    HV_TRY(tmp.get(&temp, tb));
+    HV_CUDA(cub::DeviceScan::ExclusiveSum(temp, tb, cnt64, off, (int64_t)(n + 1)));
+    uint64_t total = 0;
+    HV_CUDA(cudaMemcpy(&total, off + n, 8, cudaMemcpyDeviceToHost));
+    if (total >= (1ull << 32)) { set_error("too many segment pieces"); return HV_EINVAL; }
+    HV_TRY(dev_alloc(c, (void**)out, total * sizeof(Piece)));
+    k_emit_pieces<<<grid_for(n, 256), 256>>>(segs, n, cnt, off, *out);
+    HV_CUDA(cudaGetLastError());
+    HV_CUDA(cudaDeviceSynchronize());
+    *n_out = total;
+    *extent = (int32_t)(1u << shift);
+    return HV_OK;
+}
 
 void free_tree(Ctx* c, Tree* t) {
     if (t->nodes) dev_free(c, t->nodes, t->nodes_bytes);
@@ -263,29 +378,39 @@ int build_tree_points(Layer* L) {
     return HV_OK;
 }
 
-int build_tree_segments(Layer* L) {
+// Segments (and polygon edges) are indexed as pieces: sort the pieces by
+// the Hilbert key of their box centre and build the tree over their boxes.
+static int build_piece_tree(Layer* L, const int4* segs, uint64_t n_seg) {
     Ctx* c = L->ctx;
-    if (L->n_obj) {
-        HV_TRY(sort_objects<SegObj>(c, (int4**)&L->obj, L->n_obj, &L->keys, nullptr));
-    }
-    HV_TRY(build_levels<SegObj>(c, (const int4*)L->obj, L->n_obj, &L->tree));
+    Piece* pieces = nullptr;
+    uint64_t n = 0;
+    HV_TRY(make_pieces(c, segs, n_seg, &pieces, &n, &L->piece_extent));
+    if (L->obj) dev_free(c, L->obj, L->obj_bytes);
+    L->obj = pieces;
+    L->obj_bytes = n * sizeof(Piece);
+    L->n_obj = n;
+    if (n) HV_TRY(sort_objects<PieceObj>(c, (Piece**)&L->obj, n, &L->keys, nullptr));
+    HV_TRY(build_levels<PieceObj>(c, (const Piece*)L->obj, n, &L->tree));
+    return HV_OK;
+}
+
+int build_tree_segments(Layer* L) {
+    // the input segments are replaced by their pieces
+    int4* segs = (int4*)L->obj;
+    uint64_t n = L->n_src, bytes = L->obj_bytes;
+    L->obj = nullptr;
+    L->obj_bytes = 0;
+    int rc = build_piece_tree(L, segs, n);
+    dev_free(L->ctx, segs, bytes);
+    HV_TRY(rc);
     HV_CUDA(cudaDeviceSynchronize());
     return HV_OK;
 }
 
 int build_tree_polygons(Layer* L) {
     Ctx* c = L->ctx;
-    // the edge tree (outline): sorted copy of the polygon-order edges
-    if (L->n_obj) {
-        int4* copy;
-        HV_TRY(dev_alloc(c, (void**)&copy, L->n_obj * 16));
-        HV_CUDA(cudaMemcpy(copy, L->poly_edges, L->n_obj * 16, cudaMemcpyDeviceToDevice));
-        if (L->obj) dev_free(c, L->obj, L->obj_bytes);
-        L->obj = copy;
-        L->obj_bytes = L->n_obj * 16;
-        HV_TRY(sort_objects<SegObj>(c, (int4**)&L->obj, L->n_obj, &L->keys, nullptr));
-    }
-    HV_TRY(build_levels<SegObj>(c, (const int4*)L->obj, L->n_obj, &L->tree));
+    // the edge tree (outline) over pieces of the polygon-order edges
+    HV_TRY(build_piece_tree(L, L->poly_edges, L->n_src));
     // the polygon-box tree (fill)
     if (L->n_poly) {
         HV_TRY(sort_objects<BoxObj>(c, &L->mbr_obj, L->n_poly, &L->mbr_keys, &L->mbr_ids));
@@ -351,6 +476,7 @@ int prepare_polygons(Ctx* c, const int2* d_xy, uint64_t n_vert, const uint64_t* 
     HV_CUDA(cudaMemcpy(d_ro, h_ring_off, (n_rings + 1) * 8, cudaMemcpyHostToDevice));
     HV_CUDA(cudaMemcpy(d_pro, h_poly_ring_off, (n_polys + 1) * 8, cudaMemcpyHostToDevice));
     L->n_obj = n_vert;
+    L->n_src = n_vert;
     L->n_poly = n_polys;
     HV_TRY(dev_alloc(c, (void**)&L->poly_edges, (n_vert ? n_vert : 1) * 16));
     HV_TRY(dev_alloc(c, (void**)&L->poly_edge_off, (n_polys + 1) * 8));

@@ -37,6 +37,13 @@ struct Ctx {
 int dev_alloc(Ctx* c, void** p, uint64_t bytes);
 void dev_free(Ctx* c, void* p, uint64_t bytes);
 
+// A segment piece: the whole segment (for the exact distance test) and a
+// conservative box of the part of it the piece stands for (for pruning).
+struct __align__(16) Piece {
+    int4 seg;
+    int4 box;
+};
+
 // A packed R-tree over n objects sorted by Hilbert key.  Inner nodes hold 32
 // child boxes as SoA int32 [minx x32][miny x32][maxx x32][maxy x32] (512 B).
 // Level 1 nodes hold leaf boxes (a leaf = 32 consecutive objects), level l
@@ -101,10 +108,14 @@ struct Layer {
     Ctx* ctx = nullptr;
     int kind = HV_LAYER_POINTS;
     uint32_t indexes = 0;
-    // raw objects (input order) until the index is built, then sorted
-    uint64_t n_obj = 0;          // points, segments, or polygon edges
-    void* obj = nullptr;         // int2 points or int4 segments (sorted once built)
+    // objects: input order until the index is built, then the sorted index
+    // records (points, or segment pieces: the full segment plus the box of a
+    // bounded-extent piece of it)
+    uint64_t n_src = 0;          // points, segments or polygon edges
+    uint64_t n_obj = 0;          // index records (points or pieces)
+    void* obj = nullptr;
     uint64_t obj_bytes = 0;
+    int32_t piece_extent = 0;    // max extent of a piece (segment layers)
     uint64_t* keys = nullptr;    // sorted Hilbert keys of obj (after build)
     Tree tree;                   // R-tree over obj
     // polygons
@@ -126,6 +137,7 @@ struct Layer {
 // index build (hv_build.cu)
 int build_tree_points(Layer* L);
 int build_tree_segments(Layer* L);
+int make_pieces(Ctx* c, const int4* segs, uint64_t n, Piece** out, uint64_t* n_out, int32_t* extent);
 int build_tree_polygons(Layer* L);
 void free_tree(Ctx* c, Tree* t);
 // learned index (hv_learned.cu)

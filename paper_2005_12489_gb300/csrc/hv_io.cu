@@ -19,7 +19,7 @@ namespace hv {
 namespace {
 
 constexpr char kMagic[8] = {'H', 'V', 'L', 'A', 'Y', 'E', 'R', '\0'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr uint64_t kStage = 64ull << 20;
 
 enum Tag : uint32_t {
@@ -37,10 +37,11 @@ struct Header {
     uint32_t version;
     uint32_t kind;
     uint32_t indexes;
-    uint32_t reserved;
+    int32_t piece_extent;
     uint64_t n_obj;
     uint64_t n_poly;
     int4 mbr;
+    uint64_t n_src;
 };
 
 struct LScalars {
@@ -165,13 +166,14 @@ int hv_layer_save(hv_layer* layer, const char* path) {
     h.n_obj = L->n_obj;
     h.n_poly = L->n_poly;
     h.mbr = L->mbr;
+    h.n_src = L->n_src;
+    h.piece_extent = L->piece_extent;
     int rc = fwrite(&h, sizeof(h), 1, f) == 1 ? HV_OK : HV_EINVAL;
-    uint64_t ob = L->kind == HV_LAYER_POINTS ? 8 : 16;
-    if (rc == HV_OK && L->n_obj) rc = w.put(kObj, L->obj, L->n_obj * ob, true);
+    if (rc == HV_OK && L->n_obj) rc = w.put(kObj, L->obj, L->obj_bytes, true);
     if (rc == HV_OK && L->n_obj) rc = w.put(kKeys, L->keys, L->n_obj * 8, true);
     if (rc == HV_OK) rc = put_tree(w, kTree, kTreeNodes, L->tree);
     if (rc == HV_OK && L->kind == HV_LAYER_POLYGONS) {
-        if (L->n_obj) rc = w.put(kPolyEdges, L->poly_edges, L->n_obj * 16, true);
+        if (L->n_src) rc = w.put(kPolyEdges, L->poly_edges, L->n_src * 16, true);
         if (rc == HV_OK) rc = w.put(kPolyEdgeOff, L->poly_edge_off, (L->n_poly + 1) * 8, true);
         if (rc == HV_OK && L->n_poly) rc = w.put(kMbrObj, L->mbr_obj, L->n_poly * 16, true);
         if (rc == HV_OK && L->n_poly) rc = w.put(kMbrIds, L->mbr_ids, L->n_poly * 4, true);
@@ -208,6 +210,8 @@ int hv_layer_load_file(hv_ctx* ctx, const char* path, hv_layer** out) {
     L->n_obj = h.n_obj;
     L->n_poly = h.n_poly;
     L->mbr = h.mbr;
+    L->n_src = h.n_src;
+    L->piece_extent = h.piece_extent;
     Reader r{f, c};
     int rc = cudaMallocHost(&r.stage, kStage) == cudaSuccess ? HV_OK : HV_ECUDA;
     LScalars ls[2];

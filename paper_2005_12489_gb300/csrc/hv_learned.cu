@@ -246,19 +246,12 @@ __global__ void k_max_u32(const uint32_t* a, uint32_t n, unsigned long long* out
     }
 }
 
-// Half-extent of each object box (ceil of half the larger side) and a
-// histogram of its bit length.
-template <class T>
-__device__ __forceinline__ int4 obj_box(T o);
-template <>
-__device__ __forceinline__ int4 obj_box<int4>(int4 s) {
-    return make_int4(min(s.x, s.z), min(s.y, s.w), max(s.x, s.z), max(s.y, s.w));
-}
-
-__global__ void k_extent_hist(const int4* obj, uint64_t n, bool is_box, unsigned long long* hist) {
+// Half-extent of each record's box (half the larger side, plus one) and a
+// histogram of its bit length; boxes are read at boxes[i * stride].
+__global__ void k_extent_hist(const int4* boxes, uint32_t stride, uint64_t n, unsigned long long* hist) {
     uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int4 b = is_box ? obj[i] : obj_box<int4>(obj[i]);
+    int4 b = boxes[i * stride];
     if (b.x > b.z) return;  // empty box
     int64_t w = (int64_t)b.z - b.x, h = (int64_t)b.w - b.y;
     int64_t e = (w > h ? w : h) / 2 + 1;
@@ -266,11 +259,11 @@ __global__ void k_extent_hist(const int4* obj, uint64_t n, bool is_box, unsigned
     atomicAdd(hist + bits, 1ull);
 }
 
-__global__ void k_mark_outliers(const int4* obj, uint64_t n, bool is_box, int64_t halo, uint32_t* flag,
+__global__ void k_mark_outliers(const int4* boxes, uint32_t stride, uint64_t n, int64_t halo, uint32_t* flag,
                                 unsigned long long* count) {
     uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int4 b = is_box ? obj[i] : obj_box<int4>(obj[i]);
+    int4 b = boxes[i * stride];
     bool out = false;
     if (b.x <= b.z) {
         int64_t w = (int64_t)b.z - b.x, h = (int64_t)b.w - b.y;
@@ -280,20 +273,24 @@ __global__ void k_mark_outliers(const int4* obj, uint64_t n, bool is_box, int64_
     if (out) atomicAdd(count, 1ull);
 }
 
-__global__ void k_collect(const int4* obj, const uint32_t* ids, uint64_t n, const uint32_t* flag, int4* out,
+__global__ void k_collect(const int4* boxes, const uint32_t* ids, uint64_t n, const uint32_t* flag, int4* out,
                           uint32_t* out_ids, unsigned long long* pos) {
     uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (i >= n || !flag[i]) return;
     unsigned long long p = atomicAdd(pos, 1ull);
-    out[p] = obj[i];
+    out[p] = boxes[i];
     out_ids[p] = ids ? ids[i] : (uint32_t)i;
 }
 
 }  // namespace
 
 // Build the model over sorted keys `keys[0..n)` (objects `obj` of `kind`).
-static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const int4* boxes_or_segs,
-                     bool is_box, const uint32_t* ids, const hv_build_opts* opts, int64_t* err_out) {
+// boxes: the records' boxes at boxes[i * stride] (NULL for points: no
+// extent).  With allow_outliers the halo covers 99.5% of the records and the
+// rest go to a side tree (only for plain box records, stride 1); otherwise the
+// halo covers every record.
+static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const int4* boxes, uint32_t stride,
+                     bool allow_outliers, const uint32_t* ids, const hv_build_opts* opts, int64_t* err_out) {
     Alloc A{L, c};
     LearnedView& v = L->view;
     v = LearnedView();
@@ -420,11 +417,11 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
     v.mean_window = (use_mlp ? sum_mlp : sum_lin) / (double)n_seg;
     *err_out = v.eps;
     // halo and side tree for objects with extent
-    if (boxes_or_segs) {
+    if (boxes) {
         unsigned long long* hist;
         HV_TRY(dev_alloc(c, (void**)&hist, 65 * 8));
         cudaMemset(hist, 0, 65 * 8);
-        k_extent_hist<<<blocks_for(n, 256), 256>>>(boxes_or_segs, n, is_box, hist);
+        k_extent_hist<<<blocks_for(n, 256), 256>>>(boxes, stride, n, hist);
         unsigned long long hh[65];
         cudaError_t e = cudaMemcpy(hh, hist, 65 * 8, cudaMemcpyDeviceToHost);
         dev_free(c, hist, 65 * 8);
@@ -434,7 +431,7 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
         int bits = 0;
         for (int b = 0; b < 65; b++) {
             acc += hh[b];
-            if (acc * 1000 >= total * 995) { bits = b; break; }
+            if (allow_outliers ? acc * 1000 >= total * 995 : acc == total) { bits = b; break; }
         }
         int64_t halo = bits >= 31 ? ((int64_t)1 << 31) : ((int64_t)1 << bits);
         v.halo = (int32_t)(halo > 0x7fffffff ? 0x7fffffff : halo);
@@ -443,7 +440,7 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
         HV_TRY(dev_alloc(c, (void**)&flag, n * 4));
         HV_TRY(dev_alloc(c, (void**)&cnt, 16));
         cudaMemset(cnt, 0, 16);
-        k_mark_outliers<<<blocks_for(n, 256), 256>>>(boxes_or_segs, n, is_box, v.halo, flag, cnt);
+        k_mark_outliers<<<blocks_for(n, 256), 256>>>(boxes, stride, n, v.halo, flag, cnt);
         unsigned long long n_out = 0;
         HV_CUDA(cudaMemcpy(&n_out, cnt, 8, cudaMemcpyDeviceToHost));
         L->n_outliers = n_out;
@@ -454,7 +451,7 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
             if (rc == HV_OK) rc = dev_alloc(c, (void**)&oid, n_out * 4);
             if (rc != HV_OK) { dev_free(c, flag, n * 4); dev_free(c, cnt, 16); return rc; }
             cudaMemset(cnt + 1, 0, 8);
-            k_collect<<<blocks_for(n, 256), 256>>>(boxes_or_segs, ids, n, flag, oo, oid, cnt + 1);
+            k_collect<<<blocks_for(n, 256), 256>>>(boxes, ids, n, flag, oo, oid, cnt + 1);
             HV_CUDA(cudaGetLastError());
             int4* so;
             uint32_t* sid;
@@ -478,10 +475,12 @@ int build_learned(Layer* L, const hv_build_opts* opts) {
     Ctx* c = L->ctx;
     uint32_t max_err = opts && opts->max_error ? opts->max_error : 4096;
     int64_t e1 = 0, e2 = 0;
-    const int4* segs = L->kind == HV_LAYER_POINTS ? nullptr : (const int4*)L->obj;
-    HV_TRY(build_one(c, &L->learned, L->keys, L->n_obj, segs, false, nullptr, opts, &e1));
+    // segment pieces: their boxes follow each segment in the record, and the
+    // bounded piece extent makes every record fit the halo
+    const int4* piece_boxes = L->kind == HV_LAYER_POINTS ? nullptr : (const int4*)L->obj + 1;
+    HV_TRY(build_one(c, &L->learned, L->keys, L->n_obj, piece_boxes, 2, false, nullptr, opts, &e1));
     if (L->kind == HV_LAYER_POLYGONS)
-        HV_TRY(build_one(c, &L->mbr_learned, L->mbr_keys, L->n_poly, L->mbr_obj, true, L->mbr_ids, opts, &e2));
+        HV_TRY(build_one(c, &L->mbr_learned, L->mbr_keys, L->n_poly, L->mbr_obj, 1, true, L->mbr_ids, opts, &e2));
     if ((uint64_t)e1 > max_err || (uint64_t)e2 > max_err) {
         set_error("learned index rejected: position error bound %lld exceeds %u",
                   (long long)(e1 > e2 ? e1 : e2), max_err);

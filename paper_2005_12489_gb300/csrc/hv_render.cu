@@ -243,9 +243,14 @@ struct SegLeaf {
     __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         uint64_t i = (uint64_t)leaf * 32 + lane;
         log_read(p, kLogLeaf, leaf, lane);
+        // a record is a piece: the whole segment and the box of its piece
         int4 o = make_int4(kEmptyHi, kEmptyHi, kEmptyHi, kEmptyHi);
-        if (i < src.n) o = __ldg((const int4*)src.obj + i);
-        const int32_t sx0 = min(o.x, o.z), sy0 = min(o.y, o.w), sx1 = max(o.x, o.z), sy1 = max(o.y, o.w);
+        int4 pb = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
+        if (i < src.n) {
+            o = __ldg((const int4*)src.obj + 2 * i);
+            pb = __ldg((const int4*)src.obj + 2 * i + 1);
+        }
+        const int32_t sx0 = pb.x, sy0 = pb.y, sx1 = pb.z, sy1 = pb.w;
         uint32_t pm = rect_lanes(s, sx0, sy0, sx1, sy1) & s.U;
         if (!__any_sync(kFull, pm != 0)) return;
         const int32_t ps = 1 << s.L;

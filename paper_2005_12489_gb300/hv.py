@@ -55,7 +55,7 @@ class hv_layer_info(ctypes.Structure):
                 ("learned_error_linear", ctypes.c_int64), ("learned_error_mlp", ctypes.c_int64),
                 ("learned_mean_error", ctypes.c_double), ("learned_pieces", ctypes.c_uint32),
                 ("learned_mlp", ctypes.c_uint32), ("learned_halo", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("piece_extent", ctypes.c_int32), ("index_records", ctypes.c_uint64)]
 
 
 class hv_server_opts(ctypes.Structure):
