@@ -211,6 +211,11 @@ int hv_destroy(hv_ctx* ctx) {
     if (c->req_buf) dev_free(c, c->req_buf, c->req_cap);
     if (c->out_buf) dev_free(c, c->out_buf, c->out_cap);
     if (c->pinned_req) cudaFreeHost(c->pinned_req);
+    for (int k = 0; k < 2; k++) {
+        if (c->ev_rendered[k]) cudaEventDestroy(c->ev_rendered[k]);
+        if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     delete c;
     return HV_OK;
 }
@@ -400,14 +405,47 @@ int hv_render_tiles(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mo
         HV_CUDA(cudaMemcpyAsync(c->req_buf, reqs, rb, cudaMemcpyHostToDevice, st));
         d_reqs = (const hv_tile_req*)c->req_buf;
     }
-    uint8_t* d_out = (uint8_t*)out;
-    if (!dev_out) {
-        HV_TRY(grow(c, &c->out_buf, &c->out_cap, (uint64_t)n * tb));
-        d_out = (uint8_t*)c->out_buf;
+    if (dev_out) {
+        HV_TRY(launch_render(L, d_reqs, n, mode, index_kind, style, (uint8_t*)out, st));
+        // the request staging must be consumed before the next call reuses it
+        HV_CUDA(cudaStreamSynchronize(st));
+        return HV_OK;
     }
-    HV_TRY(launch_render(L, d_reqs, n, mode, index_kind, style, d_out, st));
-    if (!dev_out) HV_CUDA(cudaMemcpyAsync(out, d_out, (uint64_t)n * tb, cudaMemcpyDeviceToHost, st));
-    // the scratch copies above must finish before the next call reuses them
+    // Host output: render in chunks into two device buffers and copy each
+    // finished chunk to the host on a second stream while the next renders.
+    if (!c->copy_stream) {
+        HV_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; k++) {
+            HV_CUDA(cudaEventCreateWithFlags(&c->ev_rendered[k], cudaEventDisableTiming));
+            HV_CUDA(cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
+        }
+    }
+    const uint32_t chunk = n < 1024 ? n : 1024;
+    HV_TRY(grow(c, &c->out_buf, &c->out_cap, 2ull * chunk * tb));
+    uint8_t* bufs[2] = {(uint8_t*)c->out_buf, (uint8_t*)c->out_buf + (uint64_t)chunk * tb};
+    const uint32_t n_chunks = (n + chunk - 1) / chunk;
+    auto render_chunk = [&](uint32_t i) -> int {
+        uint32_t first = i * chunk, cnt = n - first < chunk ? n - first : chunk;
+        int b = i & 1;
+        HV_CUDA(cudaStreamWaitEvent(st, c->ev_copied[b], 0));   // buffer free
+        HV_TRY(launch_render(L, d_reqs + first, cnt, mode, index_kind, style, bufs[b], st));
+        HV_CUDA(cudaEventRecord(c->ev_rendered[b], st));
+        return HV_OK;
+    };
+    // fresh events are complete, so the first two waits pass at once
+    HV_CUDA(cudaEventRecord(c->ev_copied[0], c->copy_stream));
+    HV_CUDA(cudaEventRecord(c->ev_copied[1], c->copy_stream));
+    HV_TRY(render_chunk(0));
+    for (uint32_t i = 0; i < n_chunks; i++) {
+        if (i + 1 < n_chunks) HV_TRY(render_chunk(i + 1));
+        uint32_t first = i * chunk, cnt = n - first < chunk ? n - first : chunk;
+        int b = i & 1;
+        HV_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_rendered[b], 0));
+        HV_CUDA(cudaMemcpyAsync((uint8_t*)out + (uint64_t)first * tb, bufs[b], (uint64_t)cnt * tb,
+                                cudaMemcpyDeviceToHost, c->copy_stream));
+        HV_CUDA(cudaEventRecord(c->ev_copied[b], c->copy_stream));
+    }
+    HV_CUDA(cudaStreamSynchronize(c->copy_stream));
     HV_CUDA(cudaStreamSynchronize(st));
     return HV_OK;
 }

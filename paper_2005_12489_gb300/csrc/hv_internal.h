@@ -31,6 +31,9 @@ struct Ctx {
     uint64_t out_cap = 0;
     void* pinned_req = nullptr;   // pinned staging for host requests
     uint64_t pinned_req_cap = 0;
+    cudaStream_t copy_stream = nullptr;   // device -> host copies of rendered chunks
+    cudaEvent_t ev_rendered[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
     std::mutex render_mu;         // serialises use of the scratch above
 };
 

@@ -30,11 +30,9 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kStripRows = 16;
-constexpr int kStrips = kTile / kStripRows;
+constexpr int kStripRows = 16;   // the largest strip; a launch picks 4, 8 or 16 rows
 constexpr int kBW = 8, kBH = 4;
 constexpr int kBlocksX = kTile / kBW;
-constexpr int kBlocks = kBlocksX * (kStripRows / kBH);
 constexpr int kFCap = 512;
 
 // result bits per pixel
@@ -51,6 +49,8 @@ struct TreeArg {
 struct Params {
     const hv_tile_req* reqs;
     uint32_t n;
+    int rows;                   // pixel rows per CTA strip: 4, 8 or 16
+    int strips;                 // strips per tile (256 / rows)
     const uint32_t* n_dev;      // if set, the batch size is min(*n_dev, n) (graph launches)
     int mode;
     int kind;
@@ -90,7 +90,7 @@ __device__ __forceinline__ void log_read(const Params& p, uint32_t kind, uint64_
     if (p.log != nullptr && lane == 0) {
         unsigned long long k = atomicAdd(p.log_n, 1ull);
         if (k < p.log_cap)
-            p.log[k] = ((unsigned long long)(blockIdx.x / kStrips) << 38) | ((unsigned long long)kind << 35) | id;
+            p.log[k] = ((unsigned long long)(blockIdx.x / p.strips) << 38) | ((unsigned long long)kind << 35) | id;
     }
 }
 
@@ -555,17 +555,17 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         int blk = 0;
         if (lane == 0) blk = atomicAdd(&sm.next_block, 1);
         blk = __shfl_sync(kFull, blk, 0);
-        if (blk >= kBlocks) break;
+        if (blk >= kBlocksX * (p.rows / kBH)) break;
         int bx = blk % kBlocksX, by = blk / kBlocksX;
         int i = bx * kBW + (lane & 7);
         int jl = by * kBH + (lane >> 3);
-        int j = strip * kStripRows + jl;
+        int j = strip * p.rows + jl;
         Lane s;
         s.L = L;
         s.cx = X0 + i * ps + (ps >> 1);
         s.cy = Y0 + j * ps + (ps >> 1);
         s.bx0 = X0 + (bx * kBW) * ps + (ps >> 1);
-        s.by0 = Y0 + (strip * kStripRows + by * kBH) * ps + (ps >> 1);
+        s.by0 = Y0 + (strip * p.rows + by * kBH) * ps + (ps >> 1);
         s.R2 = (int64_t)R * R;
         if (V::kFill || mask_mode) {
             s.off = 0;
@@ -649,13 +649,14 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
 __global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
     __shared__ Smem sm;
     const int tid = threadIdx.x;
-    const uint32_t tile = blockIdx.x / kStrips;
-    const int strip = blockIdx.x % kStrips;
+    const int rows = p.rows;
+    const uint32_t tile = blockIdx.x / p.strips;
+    const int strip = blockIdx.x % p.strips;
     const uint32_t n = p.n_dev ? min(*p.n_dev, p.n) : p.n;
     if (tile >= n) return;
     hv_tile_req q = p.reqs[tile];
     bool ok = q.z <= 19 && q.x < (1u << q.z) && q.y < (1u << q.z) && q.r16 >= 1 && q.r16 <= 1024;
-    for (int k = tid; k < kStripRows * kTile / 4; k += kThreads) ((uint32_t*)sm.res)[k] = 0u;
+    for (int k = tid; k < rows * kTile / 4; k += kThreads) ((uint32_t*)sm.res)[k] = 0u;
     if (!ok) {
         if (tid == 0 && strip == 0) atomicOr(p.status, 1u);
     }
@@ -670,8 +671,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
         const int32_t off = mask_mode ? 0 : (ps >> 2);
         // strip sample box
         const int32_t sx0 = X0 + (ps >> 1) - off, sx1 = X0 + (kTile - 1) * ps + (ps >> 1) + off;
-        const int32_t sy0 = Y0 + strip * kStripRows * ps + (ps >> 1) - off;
-        const int32_t sy1 = Y0 + (strip * kStripRows + kStripRows - 1) * ps + (ps >> 1) + off;
+        const int32_t sy0 = Y0 + strip * rows * ps + (ps >> 1) - off;
+        const int32_t sy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1) + off;
         const bool learned = p.use_learned != 0;
         // Algorithm 1 over points / segments / polygon edges
         if (p.kind == HV_LAYER_POINTS)
@@ -683,8 +684,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
         // Algorithm 2 over polygon boxes and edges
         if (p.kind == HV_LAYER_POLYGONS) {
             const int32_t cx0 = X0 + (ps >> 1), cx1 = X0 + (kTile - 1) * ps + (ps >> 1);
-            const int32_t cy0 = Y0 + strip * kStripRows * ps + (ps >> 1);
-            const int32_t cy1 = Y0 + (strip * kStripRows + kStripRows - 1) * ps + (ps >> 1);
+            const int32_t cy0 = Y0 + strip * rows * ps + (ps >> 1);
+            const int32_t cy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1);
             stage<FillLeaf>(p, sm, p.mtree, p.mbr_obj, p.mbr_ids, p.mside, p.mside_obj, p.mside_ids,
                             learned ? &p.mlm : nullptr, p.mhalo, X0, Y0, strip, z, 0, mask_mode, cx0, cy0, cx1,
                             cy1, tid);
@@ -694,15 +695,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
     uint8_t* out = p.out + (uint64_t)tile * p.tile_bytes;
     if (p.mode == HV_MODE_MASK) {
         // 16 rows x 8 words; word w of row j = pixels 32w .. 32w+31
-        if (tid < kStripRows * 8) {
+        if (tid < rows * 8) {
             int jl = tid >> 3, w = tid & 7;
             uint32_t word = 0;
             for (int b = 0; b < 32; b++)
                 if (sm.res[jl * kTile + 32 * w + b] & (kResCentre | kResFill)) word |= 1u << b;
-            ((uint32_t*)out)[(strip * kStripRows + jl) * 8 + w] = word;
+            ((uint32_t*)out)[(strip * rows + jl) * 8 + w] = word;
         }
     } else if (p.mode == HV_MODE_COVERAGE) {
-        // 4 KB contiguous: one uint4 (16 pixels) per thread
+        // rows x 256 bytes contiguous: one uint4 (16 pixels) per thread
+        if (tid < rows * 16) {
         const uint8_t* r = sm.res + tid * 16;
         uint32_t w4[4];
         for (int k = 0; k < 4; k++) {
@@ -714,11 +716,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
             }
             w4[k] = v;
         }
-        ((uint4*)(out + (uint64_t)strip * kStripRows * kTile))[tid] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        ((uint4*)(out + (uint64_t)strip * rows * kTile))[tid] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
     } else {
-        // 16 KB contiguous: four rounds of one uint4 (4 pixels) per thread
-        uint4* o4 = (uint4*)(out + (uint64_t)strip * kStripRows * kTile * 4);
-        for (int it = 0; it < 4; it++) {
+        // rows x 1 KB contiguous: rows / 4 rounds of one uint4 (4 pixels) per thread
+        uint4* o4 = (uint4*)(out + (uint64_t)strip * rows * kTile * 4);
+        for (int it = 0; it < rows / 4; it++) {
             int px = (it * kThreads + tid) * 4;
             uint32_t w[4];
             for (int b = 0; b < 4; b++) {
@@ -809,7 +812,16 @@ int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int
         p.log_cap = log->cap;
         p.log_n = (unsigned long long*)log->count;
     }
-    uint64_t grid = (uint64_t)n * kStrips;
+    // strip height: 16 rows (16 CTAs per tile) when the batch fills the GPU,
+    // 8 or 4 rows for small batches so that a few tiles still spread over
+    // many SMs (lower latency)
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t resident = (uint64_t)sms * 4;
+    p.rows = (uint64_t)n * 16 >= 2 * resident ? 16 : ((uint64_t)n * 32 >= 2 * resident ? 8 : 4);
+    p.strips = kTile / p.rows;
+    uint64_t grid = (uint64_t)n * p.strips;
     if (grid > 0x7fffffffull) {
         set_error("too many tiles in one call");
         return HV_EINVAL;

@@ -317,3 +317,22 @@ def test_polygons_2m_sampled_tiles(ctx):
                        lambda r, m: oracle.render_polygons(xy, ro, po, r, m, STYLE_T), reqs, 6, 2)
     finally:
         hv.hv_layer_free(L)
+
+
+def test_host_output_in_chunks(ctx):
+    """More tiles than one host-output chunk (1024): the double-buffered,
+    overlapped copies must assemble exactly the device result."""
+    pts = gen.gmm_points(200_000, seed=23, k=8)
+    reqs = gen.density_tiles(pts, 2500, 4, 14, 24, seed=24)
+    L = points_layer(ctx, pts)
+    try:
+        for mode in (hv.HV_MODE_MASK, hv.HV_MODE_COVERAGE):
+            host = hv.render(L, reqs, mode, style())
+            dev = render_dev(L, reqs, mode)
+            assert np.array_equal(host, dev)
+        pinned = torch.empty((len(reqs), 8192), dtype=torch.uint8, pin_memory=True)
+        hv.hv_render_tiles(L, hv.make_requests(reqs), len(reqs), hv.HV_MODE_MASK, hv.HV_INDEX_RTREE,
+                           style(), pinned, pinned.numel(), None)
+        assert np.array_equal(pinned.numpy(), render_dev(L, reqs, hv.HV_MODE_MASK))
+    finally:
+        hv.hv_layer_free(L)
