@@ -386,7 +386,9 @@ def run_gb300(args):
                        "rtree_value": n / (rms / 1000.0), "learned_over_rtree": rms / lms,
                        "error_bound": info.learned_error, "error_bound_linear": info.learned_error_linear,
                        "error_bound_mlp": info.learned_error_mlp, "mean_error": info.learned_mean_error,
-                       "pieces": info.learned_pieces, "mlp_in_use": bool(info.learned_mlp),
+                       "pieces": info.learned_pieces, "pieces_with_mlp": info.learned_mlp,
+                       "mean_window": info.learned_mean_window,
+                       "mean_window_linear": info.learned_mean_window_linear,
                        "halo": info.learned_halo, "side_tree_objects": info.learned_outliers,
                        "train_ms": info.train_ms}
         peak, peak_kind = measured_peak_hbm()

@@ -132,12 +132,15 @@ typedef struct hv_layer_info {
     int64_t learned_error_mlp;     /* error bound with the MLP residual */
     double learned_mean_error;     /* mean |predicted - true| position */
     uint32_t learned_pieces;       /* piecewise-linear pieces */
-    uint32_t learned_mlp;          /* 1 if the MLP residual is in use */
+    uint32_t learned_mlp;          /* pieces that add the MLP residual (a piece
+                                      uses it only where it narrows its bound) */
     int32_t learned_halo;          /* half-extent covered through centre keys */
     int32_t piece_extent;          /* segment layers: segments are indexed as
                                       pieces of at most this extent */
     uint64_t index_records;        /* records in the object R-tree (points, or
                                       segment pieces) */
+    double learned_mean_window;    /* mean per-piece error bound (search window) */
+    double learned_mean_window_linear;  /* ... of the linear pieces alone */
 } hv_layer_info;
 
 /* ---- context ------------------------------------------------------------ */

@@ -341,7 +341,9 @@ int hv_layer_info_get(hv_layer* layer, hv_layer_info* out) {
         out->learned_error_mlp = lv.eps_mlp;
         out->learned_mean_error = lv.mean_err;
         out->learned_pieces = lv.n_seg;
-        out->learned_mlp = lv.hidden > 0 ? 1u : 0u;
+        out->learned_mlp = lv.hidden > 0 ? lv.pieces_mlp : 0u;
+        out->learned_mean_window = lv.mean_window;
+        out->learned_mean_window_linear = lv.mean_window_linear;
         out->learned_halo = lv.halo;
     }
     uint64_t bytes = L->obj_bytes + (L->keys ? L->n_obj * 8 : 0) + L->tree.nodes_bytes;

@@ -81,6 +81,7 @@ struct LearnedView {
     const uint32_t* radix = nullptr;    // top-bits table -> first piece
     const uint16_t* mlp = nullptr;      // bf16 MLP weights (NULL: linear only)
     const uint16_t* emb = nullptr;      // bf16 piece embeddings
+    const uint8_t* use_mlp = nullptr;   // per piece: MLP term in use
     uint32_t n_seg = 0;
     uint32_t P = 0;                     // keys per piece
     int hidden = 0;                     // MLP width, 0 = not used
@@ -88,7 +89,10 @@ struct LearnedView {
     int64_t eps_linear = 0;             // ... of the linear pieces alone
     int64_t eps_mlp = 0;                // ... with the MLP residual
     double mean_err = 0;
+    double mean_err_linear = 0;
     double mean_window = 0;             // mean per-piece bound (search window)
+    double mean_window_linear = 0;
+    uint32_t pieces_mlp = 0;            // pieces that use the MLP term
     int32_t halo = 0;                   // max half-extent of indexed objects
     uint64_t n_obj = 0;
     // objects whose extent exceeds `halo` are also kept in a small side

@@ -19,7 +19,7 @@ namespace hv {
 namespace {
 
 constexpr char kMagic[8] = {'H', 'V', 'L', 'A', 'Y', 'E', 'R', '\0'};
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;
 constexpr uint64_t kStage = 64ull << 20;
 
 enum Tag : uint32_t {
@@ -29,7 +29,7 @@ enum Tag : uint32_t {
 // learned sub-tags (added to kLearned0 / kLearned1)
 enum LTag : uint32_t {
     kLScalars = 1, kLKb, kLPa, kLPc, kLPinv, kLEps, kLRadix, kLMlp, kLEmb, kLSideTree, kLSideNodes, kLSideObj,
-    kLSideIds
+    kLSideIds, kLUse
 };
 
 struct Header {
@@ -50,6 +50,8 @@ struct LScalars {
     int64_t eps, eps_linear, eps_mlp;
     double mean_err, train_ms;
     uint64_t n_obj, n_outliers;
+    double mean_err_linear, mean_window, mean_window_linear;
+    uint32_t pieces_mlp, reserved;
 };
 
 struct Writer {
@@ -84,7 +86,7 @@ int put_learned(Writer& w, uint32_t base, const Learned& l) {
     const LearnedView& v = l.view;
     if (!v.ready) return HV_OK;
     LScalars s{v.n_seg, v.P, v.hidden, v.halo, v.eps, v.eps_linear, v.eps_mlp, v.mean_err, l.train_ms,
-               v.n_obj, l.n_outliers};
+               v.n_obj, l.n_outliers, v.mean_err_linear, v.mean_window, v.mean_window_linear, v.pieces_mlp, 0};
     HV_TRY(w.put(base + kLScalars, &s, sizeof(s), false));
     if (v.n_obj == 0) return HV_OK;
     HV_TRY(w.put(base + kLKb, v.seg_k0, (uint64_t)v.n_seg * 8, true));
@@ -93,6 +95,7 @@ int put_learned(Writer& w, uint32_t base, const Learned& l) {
     HV_TRY(w.put(base + kLPinv, v.pinv, (uint64_t)v.n_seg * 4, true));
     HV_TRY(w.put(base + kLEps, v.eps_piece, (uint64_t)v.n_seg * 4, true));
     HV_TRY(w.put(base + kLRadix, v.radix, ((1u << kRadixBits) + 2) * 4, true));
+    HV_TRY(w.put(base + kLUse, v.use_mlp, v.n_seg, true));
     if (v.hidden) {
         HV_TRY(w.put(base + kLMlp, v.mlp, kLearnNW * 2, true));
         HV_TRY(w.put(base + kLEmb, v.emb, (uint64_t)v.n_seg * 8, true));
@@ -245,7 +248,7 @@ int hv_layer_load_file(hv_ctx* ctx, const char* path, hv_layer** out) {
             default: {
                 uint32_t which = r.tag >= kLearned1 ? 1 : 0;
                 uint32_t sub = r.tag - (which ? kLearned1 : kLearned0);
-                if (r.tag < kLearned0 || sub > kLSideIds || sub == 0) {
+                if (r.tag < kLearned0 || sub > kLUse || sub == 0) {
                     set_error("hv_layer_load_file: unknown record %u", r.tag);
                     rc = HV_EINVAL;
                     break;
@@ -272,6 +275,7 @@ int hv_layer_load_file(hv_ctx* ctx, const char* path, hv_layer** out) {
                         break;
                     case kLSideObj: rc = r.device(&d, tr); v.outlier_obj = (const int4*)d; break;
                     case kLSideIds: rc = r.device(&d, tr); v.outlier_ids = (const uint32_t*)d; break;
+                    case kLUse: rc = r.device(&d, tr); v.use_mlp = (const uint8_t*)d; break;
                 }
             }
         }
@@ -297,6 +301,10 @@ int hv_layer_load_file(hv_ctx* ctx, const char* path, hv_layer** out) {
             v.eps_linear = ls[which].eps_linear;
             v.eps_mlp = ls[which].eps_mlp;
             v.mean_err = ls[which].mean_err;
+            v.mean_err_linear = ls[which].mean_err_linear;
+            v.mean_window = ls[which].mean_window;
+            v.mean_window_linear = ls[which].mean_window_linear;
+            v.pieces_mlp = ls[which].pieces_mlp;
             v.n_obj = ls[which].n_obj;
             l.train_ms = ls[which].train_ms;
             l.n_outliers = ls[which].n_outliers;

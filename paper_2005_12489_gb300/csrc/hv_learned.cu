@@ -162,11 +162,13 @@ __global__ void k_train(LModel m, const float* w, const float* emb, float* gw, f
         for (int r = 0; r < H; r++) acc = fmaf(d2[r], W2[r * H + q], acc);
         d1[q] = h1[q] > 0.f ? acc : 0.f;
     }
-    // embedding gradient (input features 1..4)
+    // embedding gradient (input features 1..4): a piece's embedding sees about
+    // one sample per step, so it takes the per-sample gradient, not the batch
+    // mean the shared weights take
     for (int q = 1; q < kLearnIn; q++) {
         float acc = 0.f;
         for (int r = 0; r < H; r++) acc = fmaf(d1[r], W1[r * kLearnIn + q], acc);
-        atomicAdd(gemb + (uint64_t)j * 4 + (q - 1), acc);
+        atomicAdd(gemb + (uint64_t)j * 4 + (q - 1), acc * (float)kBatch);
     }
     int lane = threadIdx.x & 31;
     int idx = 0;
@@ -234,6 +236,27 @@ __global__ void k_eps(LModel m, uint32_t* eps, unsigned long long* sum_err) {
 }
 
 // max and sum of the per-piece bounds (out[0] = max, out[1] = sum)
+// Keep the MLP term for a piece only where it narrows the piece's bound.
+__global__ void k_choose(const uint32_t* eps_lin, uint32_t* eps, uint8_t* use, uint32_t n_seg) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_seg) return;
+    bool u = eps[j] < eps_lin[j];
+    use[j] = u ? 1 : 0;
+    if (!u) eps[j] = eps_lin[j];
+}
+
+__global__ void k_count_u8(const uint8_t* a, uint32_t n, unsigned long long* out) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned v = (j < n && a[j]) ? 1u : 0u;
+    v = __reduce_add_sync(kFull, v);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, (unsigned long long)v);
+}
+
+__global__ void k_fill_u8(uint8_t* a, uint32_t n, uint8_t v) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) a[j] = v;
+}
+
 __global__ void k_max_u32(const uint32_t* a, uint32_t n, unsigned long long* out) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t v = i < n ? a[i] : 0u;
@@ -323,7 +346,7 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
     HV_CUDA(cudaGetLastError());
     LModel m;
     m.keys = keys; m.n = n; m.kb = kb; m.pa = pa; m.pc = pc; m.pinv = pinv; m.eps = eps; m.rt = rt;
-    m.emb = nullptr; m.w = nullptr; m.n_seg = n_seg; m.P = P; m.hidden = 0;
+    m.emb = nullptr; m.w = nullptr; m.use_mlp = nullptr; m.n_seg = n_seg; m.P = P; m.hidden = 0;
     // error of the linear pieces alone
     unsigned long long* scratch;
     HV_TRY(dev_alloc(c, (void**)&scratch, 64));
@@ -342,10 +365,18 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
         *sum_eps = (double)h[2];
         return HV_OK;
     };
-    uint32_t eps_lin = 0, eps_mlp = 0;
-    double mean_lin = 0, mean_mlp = 0, sum_lin = 0, sum_mlp = 0;
+    uint32_t eps_lin = 0, eps_mlp = 0, eps_fin = 0;
+    double mean_lin = 0, mean_mlp = 0, sum_lin = 0, sum_mlp = 0, mean_fin = 0, sum_fin = 0;
+    uint8_t* use;
+    uint32_t* eps_l;
+    HV_TRY(A.get((void**)&use, n_seg));
+    HV_TRY(A.get((void**)&eps_l, (uint64_t)n_seg * 4));
+    k_fill_u8<<<blocks_for(n_seg, 256), 256>>>(use, n_seg, 0);
+    m.use_mlp = use;
     int rc = measure(m, &eps_lin, &mean_lin, &sum_lin);
     if (rc != HV_OK) { dev_free(c, scratch, 64); return rc; }
+    HV_CUDA(cudaMemcpy(eps_l, eps, (uint64_t)n_seg * 4, cudaMemcpyDeviceToDevice));
+    eps_fin = eps_lin; mean_fin = mean_lin; sum_fin = sum_lin;
     // MLP residual, trained on the device
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
@@ -358,7 +389,7 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
               A.get((void**)&mo, nw * 4) == HV_OK && A.get((void**)&ve, nw * 4) == HV_OK &&
               A.get((void**)&emb, (uint64_t)n_seg * 16) == HV_OK && A.get((void**)&gemb, (uint64_t)n_seg * 16) == HV_OK &&
               A.get((void**)&wb, nw * 2) == HV_OK && A.get((void**)&embb, (uint64_t)n_seg * 8) == HV_OK;
-    bool use_mlp = false;
+    uint32_t pieces_mlp = 0;
     if (ok && steps > 0 && H > 0) {
         cudaMemset(gw, 0, nw * 4);
         cudaMemset(mo, 0, nw * 4);
@@ -371,21 +402,31 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
         for (int s = 0; s < steps; s++) {
             k_train<<<kBatch / 256, 256>>>(tm, w, emb, gw, gemb, s, seed);
             k_adam<<<blocks_for(nw, 256), 256>>>(w, gw, mo, ve, nw, s, 2e-3f);
-            k_sgd<<<blocks_for((uint64_t)n_seg * 4, 256), 256>>>(emb, gemb, (uint64_t)n_seg * 4, 0.5f * n_seg / (float)kBatch);
+            k_sgd<<<blocks_for((uint64_t)n_seg * 4, 256), 256>>>(emb, gemb, (uint64_t)n_seg * 4, 0.02f);
         }
         k_to_bf16<<<blocks_for(nw, 256), 256>>>(w, wb, nw);
         k_to_bf16<<<blocks_for((uint64_t)n_seg * 4, 256), 256>>>(emb, embb, (uint64_t)n_seg * 4);
         HV_CUDA(cudaGetLastError());
+        // every piece with the MLP term ...
         LModel mm = m;
         mm.hidden = H;
         mm.w = wb;
         mm.emb = embb;
+        k_fill_u8<<<blocks_for(n_seg, 256), 256>>>(use, n_seg, 1);
         rc = measure(mm, &eps_mlp, &mean_mlp, &sum_mlp);
         if (rc != HV_OK) { dev_free(c, scratch, 64); return rc; }
-        // keep the MLP when it narrows the average search window without
-        // widening the worst one by more than a quarter
-        use_mlp = sum_mlp < sum_lin && (double)eps_mlp <= 1.25 * (double)eps_lin;
-        if (use_mlp) m = mm;
+        // ... then each piece keeps the model with the narrower bound, and the
+        // bounds are measured again with the combined model
+        k_choose<<<blocks_for(n_seg, 256), 256>>>(eps_l, eps, use, n_seg);
+        rc = measure(mm, &eps_fin, &mean_fin, &sum_fin);
+        if (rc != HV_OK) { dev_free(c, scratch, 64); return rc; }
+        unsigned long long* cntd = scratch + 4;
+        HV_CUDA(cudaMemset(cntd, 0, 8));
+        k_count_u8<<<blocks_for(n_seg, 256), 256>>>(use, n_seg, cntd);
+        unsigned long long hc = 0;
+        HV_CUDA(cudaMemcpy(&hc, cntd, 8, cudaMemcpyDeviceToHost));
+        pieces_mlp = (uint32_t)hc;
+        if (pieces_mlp) m = mm;
     }
     cudaEventRecord(t1);
     cudaEventSynchronize(t1);
@@ -394,8 +435,9 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     L->train_ms += ms;
-    if (!use_mlp) {
-        rc = measure(m, &eps_lin, &mean_lin, &sum_lin);  // restore the linear bounds
+    if (!pieces_mlp) {
+        k_fill_u8<<<blocks_for(n_seg, 256), 256>>>(use, n_seg, 0);
+        rc = measure(m, &eps_fin, &mean_fin, &sum_fin);  // the linear bounds alone
         if (rc != HV_OK) { dev_free(c, scratch, 64); return rc; }
     }
     dev_free(c, scratch, 64);
@@ -405,16 +447,20 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
     v.radix = rt;
     v.mlp = (const uint16_t*)m.w;
     v.emb = (const uint16_t*)m.emb;
+    v.use_mlp = use;
     v.pinv = pinv;
     v.eps_piece = eps;
     v.n_seg = n_seg;
     v.P = P;
     v.hidden = m.hidden;
-    v.eps = use_mlp ? eps_mlp : eps_lin;
+    v.eps = eps_fin;
     v.eps_linear = eps_lin;
     v.eps_mlp = eps_mlp;
-    v.mean_err = use_mlp ? mean_mlp : mean_lin;
-    v.mean_window = (use_mlp ? sum_mlp : sum_lin) / (double)n_seg;
+    v.mean_err = mean_fin;
+    v.mean_err_linear = mean_lin;
+    v.mean_window = sum_fin / (double)n_seg;
+    v.mean_window_linear = sum_lin / (double)n_seg;
+    v.pieces_mlp = pieces_mlp;
     *err_out = v.eps;
     // halo and side tree for objects with extent
     if (boxes) {
@@ -523,6 +569,7 @@ LModel learned_model(const LearnedView& v) {
     m.rt = v.radix;
     m.emb = (const __nv_bfloat16*)v.emb;
     m.w = (const __nv_bfloat16*)v.mlp;
+    m.use_mlp = v.use_mlp;
     m.n_seg = v.n_seg;
     m.P = v.P;
     m.hidden = v.hidden;

@@ -9,7 +9,8 @@
 //   a, c   least-squares line of the piece,
 //   t      (k - kb_j) / (kb_{j+1} - kb_j), e_j a 4-vector embedding of the
 //          piece, mlp a 5 -> H -> H -> 1 ReLU network with bf16 weights and
-//          fp32 accumulation, trained on the device on the residual.
+//          fp32 accumulation, trained on the device on the residual; a piece
+//          adds the MLP term only if that narrows its own error bound.
 // Every stored key's true position lies within eps_j of its prediction
 // (measured over all keys with this same code); a lookup searches that
 // window, confirms the bracket, and falls back to a full binary search.
@@ -35,6 +36,7 @@ struct LModel {
     const uint32_t* rt;       // radix table, (1 << kRadixBits) + 2 entries
     const __nv_bfloat16* emb; // n_seg x 4
     const __nv_bfloat16* w;   // W1 [H x 5], b1 [H], W2 [H x H], b2 [H], w3 [H], b3
+    const uint8_t* use_mlp;   // per piece: 1 if the MLP residual narrows its bound
     uint32_t n_seg;
     uint32_t P;
     int hidden;               // 0 = linear pieces only, else kLearnH
@@ -99,7 +101,7 @@ __device__ __forceinline__ float learn_predict(const LModel& m, uint32_t j, uint
     uint64_t kbj = __ldg(m.kb + j);
     float x = (float)(k - kbj);
     float pos = __ldg(m.pc + j) + __ldg(m.pa + j) * x;
-    if (m.hidden > 0) {
+    if (m.hidden > 0 && __ldg(m.use_mlp + j)) {
         float t = fminf(fmaxf(x * __ldg(m.pinv + j), 0.f), 1.f);
         pos += (float)m.P * learn_mlp(m, j, t);
     }

@@ -55,7 +55,8 @@ class hv_layer_info(ctypes.Structure):
                 ("learned_error_linear", ctypes.c_int64), ("learned_error_mlp", ctypes.c_int64),
                 ("learned_mean_error", ctypes.c_double), ("learned_pieces", ctypes.c_uint32),
                 ("learned_mlp", ctypes.c_uint32), ("learned_halo", ctypes.c_int32),
-                ("piece_extent", ctypes.c_int32), ("index_records", ctypes.c_uint64)]
+                ("piece_extent", ctypes.c_int32), ("index_records", ctypes.c_uint64),
+                ("learned_mean_window", ctypes.c_double), ("learned_mean_window_linear", ctypes.c_double)]
 
 
 class hv_server_opts(ctypes.Structure):
