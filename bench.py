@@ -211,6 +211,24 @@ def cpu_baseline(lay, n_sample):
                       % (n_sample, len(reqs), lay.n_objects, lay.kind), "seconds": dt}
 
 
+def cpu_rtree_baseline(lay, n_sample):
+    """The multithreaded CPU R-tree renderer (points) on all host cores."""
+    import cpu_baseline
+    if lay.kind != "points":
+        return None
+    t0 = time.perf_counter()
+    tree = cpu_baseline.PointTree(lay.xy)
+    build_s = time.perf_counter() - t0
+    sample = lay.reqs[np.linspace(0, len(lay.reqs) - 1, n_sample).astype(np.int64)]
+    t0 = time.perf_counter()
+    _, threads = tree.render_rgba(sample, STYLE_T[:3])
+    dt = time.perf_counter() - t0
+    tree.close()
+    return {"value": n_sample / dt, "unit": "tiles/s", "cores": threads, "kind": "cpu packed R-tree, per-sample queries",
+            "sample": "%d of the %d tiles (evenly spaced), all %d points" % (n_sample, len(lay.reqs), lay.n_objects),
+            "build_s": build_s, "seconds": dt}
+
+
 def run_reference(args):
     """The oracle as the reference arm, on the host cores (rank 0 only)."""
     rank, world, _ = dist_env()
@@ -416,6 +434,7 @@ def run_gb300(args):
                    "path": "hv_render_tiles with host requests and pinned host output"}
         n_cpu = args.cpu_sample_tiles or {2: 48, 3: 16, 4: 6}[args.config]
         cpu = None if args.no_cpu_baseline else cpu_baseline(lay, n_cpu)
+        cpu_mt = None if args.no_cpu_baseline else cpu_rtree_baseline(lay, 96)
         line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
@@ -425,7 +444,7 @@ def run_gb300(args):
                                l2="flushed between steps (512 MiB write); layer and 2.6 GB output exceed L2",
                                parallelism="replicas" if world > 1 else "single GPU"),
                 "pixel_queries_per_s": value * 65536,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "cpu_rtree_mt": cpu_mt, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                 "index_timed": args.index, "learned": learned, "latency": lat,
                 "wall_s_timed_region": wall, "step_ms": step_ms,
