@@ -34,6 +34,7 @@ constexpr int kStripRows = 16;   // the largest strip; a launch picks 4, 8 or 16
 constexpr int kBW = 8, kBH = 4;
 constexpr int kBlocksX = kTile / kBW;
 constexpr int kFCap = 512;
+constexpr int kBucketCap = 2048;   // keeps the static shared memory under 48 KiB
 
 // result bits per pixel
 constexpr uint32_t kResCentre = 16u, kResFill = 32u;
@@ -102,6 +103,12 @@ struct Smem {
     uint32_t stk_node[kWarps][kMaxLevels + 1];
     uint32_t stk_mask[kWarps][kMaxLevels + 1];
     uint32_t lanemask[kWarps][kMaxLevels + 1][32];
+    // the frontier binned by 8-pixel block column: bucket c lists the entries
+    // that can reach blocks of column c
+    uint16_t bucket[kBucketCap];
+    int bucket_off[kBlocksX + 1];
+    int bucket_cur[kBlocksX];
+    int binned;
     int f_count, f_level, f_buf, next_count, next_block;
 };
 
@@ -152,17 +159,17 @@ __device__ __forceinline__ void apply_cover(Lane& s, uint32_t c0, uint32_t c1, u
 // any object inside the box to cover any of that lane's samples.
 __device__ __forceinline__ uint32_t rect_lanes(const Lane& s, int32_t x0, int32_t y0, int32_t x1,
                                                int32_t y1) {
-    int64_t ax = (int64_t)x0 - s.ext - s.bx0, bx = (int64_t)x1 + s.ext - s.bx0;
-    int64_t ay = (int64_t)y0 - s.ext - s.by0, by = (int64_t)y1 + s.ext - s.by0;
-    int64_t c0 = -((-ax) >> s.L), c1 = bx >> s.L;
-    int64_t r0 = -((-ay) >> s.L), r1 = by >> s.L;
-    c0 = c0 < 0 ? 0 : c0;
-    r0 = r0 < 0 ? 0 : r0;
-    c1 = c1 > 7 ? 7 : c1;
-    r1 = r1 > 3 ? 3 : r1;
+    // empty boxes and padding records lie outside the grid
+    if (x0 > x1 || y0 > y1 || x0 < -kGridHalf || y0 < -kGridHalf) return 0u;
+    // differences from the block origin fit 32 bits once clamped to +-2^30
+    // (the reach is below 2^30, so farther boxes stay out of range)
+    const int32_t ax = max(x0 - s.bx0, -kGridHalf) - s.ext, bx = min(x1 - s.bx0, kGridHalf) + s.ext;
+    const int32_t ay = max(y0 - s.by0, -kGridHalf) - s.ext, by = min(y1 - s.by0, kGridHalf) + s.ext;
+    const int32_t c0 = max(-((-ax) >> s.L), 0), c1 = min(bx >> s.L, 7);
+    const int32_t r0 = max(-((-ay) >> s.L), 0), r1 = min(by >> s.L, 3);
     if (c0 > c1 || r0 > r1) return 0u;
-    uint32_t col = (0xFFu << (int)c0) & (0xFFu >> (7 - (int)c1));
-    uint32_t rows = (0x01010101u << (8 * (int)r0)) & (0x01010101u >> (8 * (3 - (int)r1)));
+    uint32_t col = (0xFFu << c0) & (0xFFu >> (7 - c1));
+    uint32_t rows = (0x01010101u << (8 * r0)) & (0x01010101u >> (8 * (3 - r1)));
     return col * rows;
 }
 
@@ -542,6 +549,54 @@ __device__ void learned_cull(const Params& p, const TreeArg& t, const LModel& m,
     refine(p, t, false, sm, bx0, by0, bx1, by1, tid);
 }
 
+// Column range [c0, c1] of 8-pixel block columns an entry box can reach: a
+// column's samples span x in [X0 + 8c ps + ps/2 - off, X0 + (8c+7) ps + ps/2
+// + off], widened by R.
+__device__ __forceinline__ void entry_columns(int4 b, int32_t X0, int L, int32_t reach, int* c0, int* c1) {
+    const int64_t base = (int64_t)X0 + ((int64_t)1 << L >> 1);
+    int64_t lo = (int64_t)b.x - reach - base - 7 * ((int64_t)1 << L);
+    int64_t hi = (int64_t)b.z + reach - base;
+    int64_t a = -((-lo) >> (L + 3)), e = hi >> (L + 3);
+    *c0 = (int)(a < 0 ? 0 : (a > kBlocksX ? kBlocksX : a));
+    *c1 = (int)(e > kBlocksX - 1 ? kBlocksX - 1 : (e < -1 ? -1 : e));
+}
+
+// Bin the frontier by block column (falls back to the whole frontier when
+// the lists would overflow).
+__device__ void bin_frontier(Smem& sm, int32_t X0, int L, int32_t reach, int tid) {
+    const int f_count = sm.f_count, fb = sm.f_buf;
+    if (tid < kBlocksX) {
+        sm.bucket_off[tid] = 0;
+        sm.bucket_cur[tid] = 0;
+    }
+    __syncthreads();
+    for (int e = tid; e < f_count; e += kThreads) {
+        int c0, c1;
+        entry_columns(sm.fbox[fb][e], X0, L, reach, &c0, &c1);
+        for (int c = c0; c <= c1; c++) atomicAdd(&sm.bucket_off[c], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int sum = 0;
+        for (int c = 0; c < kBlocksX; c++) {
+            int n = sm.bucket_off[c];
+            sm.bucket_off[c] = sum;
+            sum += n;
+        }
+        sm.bucket_off[kBlocksX] = sum;
+        sm.binned = sum <= kBucketCap;
+    }
+    __syncthreads();
+    if (sm.binned) {
+        for (int e = tid; e < f_count; e += kThreads) {
+            int c0, c1;
+            entry_columns(sm.fbox[fb][e], X0, L, reach, &c0, &c1);
+            for (int c = c0; c <= c1; c++) sm.bucket[sm.bucket_off[c] + atomicAdd(&sm.bucket_cur[c], 1)] = (uint16_t)e;
+        }
+    }
+    __syncthreads();
+}
+
 // Process every pixel block of the strip: against the culled frontier (R-tree)
 // or through the learned lookup.
 template <class V>
@@ -581,11 +636,16 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         for (int k = 0; k < 4; k++) s.Uk[k] = k < s.nk ? kFull : 0u;
         uint32_t und0 = s.und;
         {
-            for (int c0 = 0; c0 < f_count && s.U; c0 += 32) {
-                int e = c0 + lane;
+            // this block's column list, or the whole frontier
+            const bool binned = sm.binned;
+            const int lbeg = binned ? sm.bucket_off[bx] : 0;
+            const int lcnt = binned ? sm.bucket_off[bx + 1] - lbeg : f_count;
+            for (int c0 = 0; c0 < lcnt && s.U; c0 += 32) {
+                int e = -1;
                 uint32_t cm = 0;
                 int4 fbx = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
-                if (e < f_count) {
+                if (c0 + lane < lcnt) {
+                    e = binned ? (int)sm.bucket[lbeg + c0 + lane] : c0 + lane;
                     fbx = sm.fbox[fb][e];
                     cm = rect_lanes(s, fbx.x, fbx.y, fbx.z, fbx.w);
                 }
@@ -593,7 +653,7 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                 while (mm) {
                     int k = __ffs(mm) - 1;
                     mm &= mm - 1;
-                    uint32_t id = sm.fid[fb][c0 + k];
+                    uint32_t id = sm.fid[fb][__shfl_sync(kFull, e, k)];
                     if (f_level == 0) {
                         V::visit(p, src, id, s, lane);
                     } else {
@@ -638,6 +698,10 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
         learned_cull(p, t, *m, halo, sm, bx0, by0, bx1, by1, tid);
     int4 sb = st.root_box;
     bool side_hit = st.top > 0 && sb.x <= bx1 && sb.z >= bx0 && sb.y <= by1 && sb.w >= by0;
+    if (sm.f_count > 0) {
+        const int32_t off = (V::kFill || mask_mode) ? 0 : ((1 << (23 - z)) >> 2);
+        bin_frontier(sm, X0, 23 - z, (V::kFill ? 0 : R) + off, tid);
+    }
     if (sm.f_count > 0 || side_hit) {
         Src src{obj, ids, t.n_obj, t.nodes, sm.lvl_base[0]};
         Src side{sobj, sids, st.n_obj, st.nodes, sm.lvl_base[1]};
