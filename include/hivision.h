@@ -229,7 +229,9 @@ int hv_render_tiles(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mo
                     void* stream);
 
 /* Read and clear the layer's sticky device status (bit 0: an invalid device
- * request was seen).  Synchronises `stream`. */
+ * request was seen; bit 1: an internal bounds check in the render kernel
+ * failed and an access was skipped -- hv_last_error() then names the check and
+ * the offending value).  Synchronises `stream`. */
 int hv_layer_take_status(hv_layer* layer, void* stream, uint32_t* status);
 
 /* Instrumented hv_render_tiles for measurement (not for production use):

@@ -145,14 +145,15 @@ void free_layer(Layer* L) {
     }
     free_learned(c, &L->learned);
     free_learned(c, &L->mbr_learned);
-    if (L->status) dev_free(c, L->status, 4);
+    if (L->status) dev_free(c, L->status, 16);
     for (auto& a : L->extra) dev_free(c, a.first, a.second);
     delete L;
 }
 
 int finish_layer(Layer* L, hv_layer** out) {
-    int rc = dev_alloc(L->ctx, (void**)&L->status, 4);
-    if (rc == HV_OK && cudaMemset(L->status, 0, 4) != cudaSuccess) rc = HV_ECUDA;
+    // status word, pad, and the record of the first failed internal check
+    int rc = dev_alloc(L->ctx, (void**)&L->status, 16);
+    if (rc == HV_OK && cudaMemset(L->status, 0, 16) != cudaSuccess) rc = HV_ECUDA;
     if (rc != HV_OK) { free_layer(L); return rc; }
     *out = (hv_layer*)L;
     return HV_OK;
@@ -498,9 +499,15 @@ int hv_layer_take_status(hv_layer* layer, void* stream, uint32_t* status) {
     Layer* L = (Layer*)layer;
     cudaStream_t st = (cudaStream_t)stream;
     HV_CUDA(cudaSetDevice(L->ctx->device));
-    HV_CUDA(cudaMemcpyAsync(status, L->status, 4, cudaMemcpyDeviceToHost, st));
-    HV_CUDA(cudaMemsetAsync(L->status, 0, 4, st));
+    uint32_t h[4] = {0, 0, 0, 0};
+    HV_CUDA(cudaMemcpyAsync(h, L->status, 16, cudaMemcpyDeviceToHost, st));
+    HV_CUDA(cudaMemsetAsync(L->status, 0, 16, st));
     HV_CUDA(cudaStreamSynchronize(st));
+    *status = h[0];
+    if (h[0] & 2u) {
+        unsigned long long rec = (unsigned long long)h[2] | ((unsigned long long)h[3] << 32);
+        set_error("internal check %llu failed at value %llu", rec >> 56, rec & ((1ull << 56) - 1));
+    }
     return HV_OK;
 }
 

@@ -312,8 +312,8 @@ int hv_layer_load_file(hv_ctx* ctx, const char* path, hv_layer** out) {
             v.ready = true;
         }
         if (h.indexes & HV_INDEX_LEARNED) L->indexes |= HV_INDEX_LEARNED;
-        rc = dev_alloc(c, (void**)&L->status, 4);
-        if (rc == HV_OK && cudaMemset(L->status, 0, 4) != cudaSuccess) rc = HV_ECUDA;
+        rc = dev_alloc(c, (void**)&L->status, 16);
+        if (rc == HV_OK && cudaMemset(L->status, 0, 16) != cudaSuccess) rc = HV_ECUDA;
     }
     if (rc != HV_OK) {
         free_layer_public(L);

@@ -42,6 +42,7 @@ constexpr uint32_t kResCentre = 16u, kResFill = 32u;
 struct TreeArg {
     const int32_t* nodes;
     uint64_t level_off[kMaxLevels + 1];
+    uint64_t level_n[kMaxLevels + 1];
     int top;
     uint64_t n_obj;
     int4 root_box;
@@ -66,7 +67,9 @@ struct Params {
     const uint32_t* mbr_ids;
     const int4* poly_edges;
     const uint64_t* poly_edge_off;
-    uint32_t* status;
+    uint32_t* status;                 // bit 0: invalid request; bit 1: internal check failed
+    unsigned long long* fault;        // first failed check: code << 56 | value
+    uint64_t n_poly, n_edges;
     // learned candidate lookup (use_learned): models over the sorted keys of
     // the objects and of the polygon boxes, their halos and side trees
     int use_learned;
@@ -95,11 +98,20 @@ __device__ __forceinline__ void log_read(const Params& p, uint32_t kind, uint64_
     }
 }
 
+// Bounds checks on every index the traversal follows: a failure records the
+// first offending value and the access is skipped (the tile is then wrong,
+// never the memory).
+__device__ __noinline__ void check_failed(const Params& p, uint32_t code, uint64_t v) {
+    atomicCAS(p.fault, 0ull, ((unsigned long long)code << 56) | (v & ((1ull << 56) - 1)));
+    atomicOr(p.status, 2u);
+}
+
 struct Smem {
     uint8_t res[kStripRows * kTile];
     int4 fbox[2][kFCap];
     uint32_t fid[2][kFCap];
     const int32_t* lvl_base[2][kMaxLevels + 1];   // [0]: tree being traversed, [1]: its side tree
+    uint32_t lvl_n[2][kMaxLevels + 1];            // nodes per level
     uint32_t stk_node[kWarps][kMaxLevels + 1];
     uint32_t stk_mask[kWarps][kMaxLevels + 1];
     uint32_t lanemask[kWarps][kMaxLevels + 1][32];
@@ -120,6 +132,7 @@ struct Src {
     uint64_t n;
     const int32_t* nodes;        // node array (for the read log)
     const int32_t* const* lvl;   // lvl[l] = first node of level l
+    const uint32_t* lvl_n;       // lvl_n[l] = nodes of level l
 };
 
 // Per-lane state of one 8 x 4 pixel block (lane l = pixel (l & 7, l >> 3)).
@@ -220,6 +233,10 @@ __device__ __forceinline__ bool reaches(const Lane& s, bool fill, uint32_t cm, i
 struct PointLeaf {
     static constexpr bool kFill = false;
     __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
+        if ((uint64_t)leaf * 32 >= src.n) {
+            if (lane == 0) check_failed(p, 4, leaf);
+            return;
+        }
         uint64_t i = (uint64_t)leaf * 32 + lane;
         log_read(p, kLogLeaf, leaf, lane);
         int2 o = make_int2(kEmptyHi, kEmptyHi);
@@ -248,6 +265,10 @@ struct PointLeaf {
 struct SegLeaf {
     static constexpr bool kFill = false;
     __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
+        if ((uint64_t)leaf * 32 >= src.n) {
+            if (lane == 0) check_failed(p, 4, leaf);
+            return;
+        }
         uint64_t i = (uint64_t)leaf * 32 + lane;
         log_read(p, kLogLeaf, leaf, lane);
         // a record is a piece: the whole segment and the box of its piece
@@ -284,6 +305,10 @@ struct SegLeaf {
 struct FillLeaf {
     static constexpr bool kFill = true;
     __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
+        if ((uint64_t)leaf * 32 >= src.n) {
+            if (lane == 0) check_failed(p, 4, leaf);
+            return;
+        }
         uint64_t i = (uint64_t)leaf * 32 + lane;
         log_read(p, kLogPolyLeaf, leaf, lane);
         int4 b = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
@@ -303,7 +328,15 @@ struct FillLeaf {
             bool active = s.und && s.cx >= bx0 && s.cx <= bx1 && s.cy >= by0 && s.cy <= by1;
             if (__ballot_sync(kFull, active) == 0) continue;
             log_read(p, kLogPoly, pid, lane);
+            if (pid >= p.n_poly) {
+                if (lane == 0) check_failed(p, 5, pid);
+                continue;
+            }
             uint64_t e0 = __ldg(p.poly_edge_off + pid), e1 = __ldg(p.poly_edge_off + pid + 1);
+            if (e0 > e1 || e1 > p.n_edges) {
+                if (lane == 0) check_failed(p, 6, ((uint64_t)pid << 24) | (e1 & 0xffffff));
+                continue;
+            }
             uint32_t parity = 0;
             for (uint64_t base = e0; base < e1; base += 32) {
                 int4 e = make_int4(0, 0, 0, 0);
@@ -349,6 +382,10 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
     uint32_t* stk_node = sm.stk_node[warp];
     uint32_t* stk_mask = sm.stk_mask[warp];
     int lvl = level;
+    if (level < 1 || level > kMaxLevels || node >= src.lvl_n[level]) {
+        if (lane == 0) check_failed(p, 2, ((uint64_t)level << 40) | node);
+        return;
+    }
     uint32_t m0 = child_hits(p, V::kFill, src, src.lvl[lvl] + (uint64_t)node * 128, s, lane,
                              sm.lanemask[warp][lvl]);
     stk_node[lvl] = node;
@@ -371,6 +408,10 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
             V::visit(p, src, child, s, lane);
             if (s.U == 0) return;
         } else {
+            if (child >= src.lvl_n[lvl - 1]) {
+                if (lane == 0) check_failed(p, 3, ((uint64_t)(lvl - 1) << 40) | child);
+                continue;
+            }
             lvl--;
             uint32_t hm = child_hits(p, V::kFill, src, src.lvl[lvl] + (uint64_t)child * 128, s, lane,
                                      sm.lanemask[warp][lvl]);
@@ -386,7 +427,11 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
 __device__ __forceinline__ void set_levels(Smem& sm, int slot, const TreeArg& t, int tid) {
 #pragma unroll
     for (int l = 0; l <= kMaxLevels; l++)
-        if (tid == l) sm.lvl_base[slot][l] = (l >= 1 && l <= t.top) ? t.nodes + t.level_off[l] * 128 : nullptr;
+        if (tid == l) {
+            sm.lvl_base[slot][l] = (l >= 1 && l <= t.top) ? t.nodes + t.level_off[l] * 128 : nullptr;
+            // level 0 counts leaves
+            sm.lvl_n[slot][l] = l == 0 ? (uint32_t)((t.n_obj + 31) / 32) : (l <= t.top ? (uint32_t)t.level_n[l] : 0u);
+        }
 }
 
 // Refine the shared frontier breadth first: replace every entry by its
@@ -403,6 +448,10 @@ __device__ void refine(const Params& p, const TreeArg& t, bool fill, Smem& sm, i
         const int32_t* base = sm.lvl_base[0][lvl];
         for (int e = warp; e < cnt; e += kWarps) {
             uint32_t node = sm.fid[cur][e];
+            if (node >= sm.lvl_n[0][lvl]) {
+                if (lane == 0) check_failed(p, 8, ((uint64_t)lvl << 40) | node);
+                continue;
+            }
             const int32_t* nd = base + (uint64_t)node * 128;
             if (p.log != nullptr)
                 log_read(p, fill ? kLogPolyNode : kLogNode, (uint64_t)(nd - t.nodes) >> 7, lane);
@@ -591,7 +640,10 @@ __device__ void bin_frontier(Smem& sm, int32_t X0, int L, int32_t reach, int tid
         for (int e = tid; e < f_count; e += kThreads) {
             int c0, c1;
             entry_columns(sm.fbox[fb][e], X0, L, reach, &c0, &c1);
-            for (int c = c0; c <= c1; c++) sm.bucket[sm.bucket_off[c] + atomicAdd(&sm.bucket_cur[c], 1)] = (uint16_t)e;
+            for (int c = c0; c <= c1; c++) {
+                int pos = sm.bucket_off[c] + atomicAdd(&sm.bucket_cur[c], 1);
+                if (pos < sm.bucket_off[c + 1]) sm.bucket[pos] = (uint16_t)e;
+            }
         }
     }
     __syncthreads();
@@ -646,8 +698,13 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                 int4 fbx = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
                 if (c0 + lane < lcnt) {
                     e = binned ? (int)sm.bucket[lbeg + c0 + lane] : c0 + lane;
-                    fbx = sm.fbox[fb][e];
-                    cm = rect_lanes(s, fbx.x, fbx.y, fbx.z, fbx.w);
+                    if (e >= f_count) {
+                        check_failed(p, 1, ((uint64_t)bx << 32) | (uint32_t)e);
+                        e = -1;
+                    } else {
+                        fbx = sm.fbox[fb][e];
+                        cm = rect_lanes(s, fbx.x, fbx.y, fbx.z, fbx.w);
+                    }
                 }
                 uint32_t mm = __ballot_sync(kFull, reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
                 while (mm) {
@@ -703,8 +760,8 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
         bin_frontier(sm, X0, 23 - z, (V::kFill ? 0 : R) + off, tid);
     }
     if (sm.f_count > 0 || side_hit) {
-        Src src{obj, ids, t.n_obj, t.nodes, sm.lvl_base[0]};
-        Src side{sobj, sids, st.n_obj, st.nodes, sm.lvl_base[1]};
+        Src src{obj, ids, t.n_obj, t.nodes, sm.lvl_base[0], sm.lvl_n[0]};
+        Src side{sobj, sids, st.n_obj, st.nodes, sm.lvl_base[1], sm.lvl_n[1]};
         blocks_pass<V>(p, sm, src, side, side_hit ? st.top : 0, X0, Y0, strip, z, R, mask_mode, tid);
     }
     __syncthreads();
@@ -811,7 +868,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
 TreeArg tree_arg(const TreeView& v) {
     TreeArg a;
     a.nodes = v.nodes;
-    for (int l = 0; l <= kMaxLevels; l++) a.level_off[l] = v.level_off[l];
+    for (int l = 0; l <= kMaxLevels; l++) {
+        a.level_off[l] = v.level_off[l];
+        a.level_n[l] = v.level_n[l];
+    }
     a.top = v.top;
     a.n_obj = v.n_obj;
     a.root_box = v.root_box;
@@ -850,6 +910,9 @@ int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int
     p.poly_edges = L->poly_edges;
     p.poly_edge_off = L->poly_edge_off;
     p.status = L->status;
+    p.fault = (unsigned long long*)(L->status + 2);
+    p.n_poly = L->n_poly;
+    p.n_edges = L->n_src;
     if (index_kind == HV_INDEX_LEARNED) {
         const LearnedView& a = L->learned.view;
         const LearnedView& b = L->mbr_learned.view;
