@@ -125,7 +125,7 @@ typedef struct hv_layer_info {
     uint64_t device_bytes;       /* device memory held by the layer */
     int64_t learned_error;       /* learned index: max |predicted - true| position
                                     (-1: not built) */
-    uint64_t learned_outliers;   /* learned index: objects kept in the side tree */
+    uint64_t learned_outliers;   /* learned index: records kept in side trees (objects and polygon boxes) */
     double build_ms;             /* last index build, device time */
     double train_ms;             /* learned-index training, device time */
     int64_t learned_error_linear;  /* error bound of the linear pieces alone */

@@ -333,7 +333,7 @@ int hv_layer_info_get(hv_layer* layer, hv_layer_info* out) {
     out->tree_levels = L->tree.view.top;
     out->tree_nodes = L->tree.n_nodes;
     out->learned_error = L->learned.view.ready ? L->learned.view.eps : -1;
-    out->learned_outliers = L->learned.n_outliers;
+    out->learned_outliers = L->learned.n_outliers + L->mbr_learned.n_outliers;
     out->build_ms = L->build_ms;
     out->train_ms = L->learned.train_ms + L->mbr_learned.train_ms;
     const LearnedView& lv = L->learned.view;

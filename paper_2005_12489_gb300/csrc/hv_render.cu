@@ -572,7 +572,9 @@ __device__ void learned_cull(const Params& p, const TreeArg& t, const LModel& m,
     if (a <= b) {
         uint64_t e0 = a >> (5 * lvl), e1 = b >> (5 * lvl);
         const int32_t* par = sm.lvl_base[0][lvl + 1];
-        for (uint64_t e = e0; e <= e1; e++) {
+        const bool inside = (e1 >> 5) < sm.lvl_n[0][lvl + 1];
+        if (!inside) check_failed(p, 9, ((uint64_t)lvl << 40) | (e1 & ((1ull << 40) - 1)));
+        for (uint64_t e = e0; inside && e <= e1; e++) {
             const int32_t* nd = par + (e >> 5) * 128;
             int c = (int)(e & 31);
             int4 bb = make_int4(__ldg(nd + c), __ldg(nd + 32 + c), __ldg(nd + 64 + c), __ldg(nd + 96 + c));
@@ -690,8 +692,13 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         {
             // this block's column list, or the whole frontier
             const bool binned = sm.binned;
-            const int lbeg = binned ? sm.bucket_off[bx] : 0;
-            const int lcnt = binned ? sm.bucket_off[bx + 1] - lbeg : f_count;
+            int lbeg = binned ? sm.bucket_off[bx] : 0;
+            int lcnt = binned ? sm.bucket_off[bx + 1] - lbeg : f_count;
+            if (binned && (lbeg < 0 || lcnt < 0 || lbeg + lcnt > kBucketCap)) {
+                if (lane == 0) check_failed(p, 7, ((uint64_t)bx << 32) | (uint32_t)lbeg);
+                lbeg = 0;
+                lcnt = 0;
+            }
             for (int c0 = 0; c0 < lcnt && s.U; c0 += 32) {
                 int e = -1;
                 uint32_t cm = 0;
@@ -755,11 +762,12 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
         learned_cull(p, t, *m, halo, sm, bx0, by0, bx1, by1, tid);
     int4 sb = st.root_box;
     bool side_hit = st.top > 0 && sb.x <= bx1 && sb.z >= bx0 && sb.y <= by1 && sb.w >= by0;
-    if (sm.f_count > 0) {
+    if (sm.f_count > 0 || side_hit) {
+        // the column lists are rebuilt for every pass, also for an empty
+        // frontier (a strip reached only by the side tree), so that the
+        // blocks never read the lists of an earlier stage
         const int32_t off = (V::kFill || mask_mode) ? 0 : ((1 << (23 - z)) >> 2);
         bin_frontier(sm, X0, 23 - z, (V::kFill ? 0 : R) + off, tid);
-    }
-    if (sm.f_count > 0 || side_hit) {
         Src src{obj, ids, t.n_obj, t.nodes, sm.lvl_base[0], sm.lvl_n[0]};
         Src side{sobj, sids, st.n_obj, st.nodes, sm.lvl_base[1], sm.lvl_n[1]};
         blocks_pass<V>(p, sm, src, side, side_hit ? st.top : 0, X0, Y0, strip, z, R, mask_mode, tid);

@@ -164,6 +164,38 @@ def test_learned_polygon_tiles(ctx):
         hv.hv_layer_free(L)
 
 
+def test_learned_polygon_outliers(ctx):
+    """A few very large polygons among small ones: their boxes exceed the
+    learned halo and live in the side tree, so strips deep inside them have
+    an empty learned frontier in both stages and are filled through the side
+    tree alone."""
+    xy, ro, po = gen.star_polygons(3_000, seed=73, k=8, rho_median=6e-4)
+    cen = gen.polygon_centres(xy, ro, po)[:12].astype(np.int64)
+    h = 1 << 25
+    sq = np.stack([np.stack([cen[:, 0] - h, cen[:, 1] - h], 1), np.stack([cen[:, 0] + h, cen[:, 1] - h], 1),
+                   np.stack([cen[:, 0] + h, cen[:, 1] + h], 1), np.stack([cen[:, 0] - h, cen[:, 1] + h], 1)], 1)
+    sq = np.clip(sq, -(1 << 30), (1 << 30) - 1).reshape(-1, 2).astype(np.int32)
+    xy2 = np.concatenate([xy, sq])
+    ro2 = np.concatenate([ro, ro[-1] + 4 * np.arange(1, 13, dtype=np.uint64)]).astype(np.uint64)
+    po2 = np.concatenate([po, po[-1] + np.arange(1, 13, dtype=np.uint64)]).astype(np.uint64)
+    # tiles inside the large squares, far from any of their edges, and tiles
+    # over the small polygons
+    reqs = np.concatenate([gen.density_tiles(cen + 12345, 12, 11, 14, [1, 8, 24], seed=75),
+                           gen.density_tiles(gen.polygon_centres(xy, ro, po), 8, 3, 12, [8, 24], seed=76)])
+    L = hv.hv_layer_load_polygons(ctx, xy2, ro2, po2)
+    hv.hv_layer_build_index(L, hv.HV_INDEX_RTREE | hv.HV_INDEX_LEARNED)
+    try:
+        assert hv.info_dict(L)["learned_outliers"] > 0
+        want = {mode: oracle.render_polygons(xy2, ro2, po2, reqs, mode, STYLE_T) for mode in MODES}
+        for mode in MODES:
+            for index in (hv.HV_INDEX_LEARNED, hv.HV_INDEX_RTREE):
+                got = render_dev(L, reqs, mode, index)
+                assert hv.hv_layer_take_status(L) == 0
+                assert np.array_equal(got, want[mode])
+    finally:
+        hv.hv_layer_free(L)
+
+
 def test_error_bound_gate(ctx):
     pts = gen.gmm_points(200_000, seed=40, k=8)
     L = hv.hv_layer_load_points(ctx, pts)
