@@ -148,6 +148,7 @@ struct Lane {
     uint32_t U;            // warp-uniform: lanes with an undecided sample
     int nk;                // samples per lane (1 or 4)
     int32_t bx0, by0;      // warp-uniform: centre of the block's first pixel
+    int32_t q;             // certain-cover half-side floor(R / sqrt 2) (points), else -1
     int L;                 // warp-uniform: log2 of the pixel size
 };
 
@@ -216,6 +217,45 @@ __device__ __forceinline__ bool round_reach(const Lane& s, int32_t x0, int32_t y
     return false;
 }
 
+// Samples that a non-empty box of points certainly covers: a sample within
+// Chebyshev distance q of every point of the box, with 2 q^2 <= R^2, is
+// within Euclidean distance R of each of them, whatever the points are.  Per
+// sample k, the lanes whose sample k lies in [x1 - q, x0 + q] x [y1 - q,
+// y0 + q] (undecided ones only).  Exact: no sample is marked that the
+// predicate would not cover, so no output depends on it.
+__device__ __forceinline__ void certain_lanes(const Lane& s, int32_t x0, int32_t y0, int32_t x1, int32_t y1,
+                                              uint32_t m[4]) {
+    m[0] = m[1] = m[2] = m[3] = 0u;
+    if (x0 > x1 || y0 > y1 || x0 < -kGridHalf || y0 < -kGridHalf) return;
+    // clamping the differences only narrows the interval (conservative)
+    const int32_t lx = max(x1 - s.bx0, -kGridHalf) - s.q, hx = min(x0 - s.bx0, kGridHalf) + s.q;
+    const int32_t ly = max(y1 - s.by0, -kGridHalf) - s.q, hy = min(y0 - s.by0, kGridHalf) + s.q;
+    if (lx > hx || ly > hy) return;   // the box is wider than 2q
+    uint32_t col[2], row[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        // sample offset -off (k = 0) or +off (k = 1) from the pixel centre
+        const int32_t o = k ? -s.off : s.off;
+        const int32_t c0 = max(-((-(lx + o)) >> s.L), 0), c1 = min((hx + o) >> s.L, 7);
+        const int32_t r0 = max(-((-(ly + o)) >> s.L), 0), r1 = min((hy + o) >> s.L, 3);
+        col[k] = c0 > c1 ? 0u : (0xFFu << c0) & (0xFFu >> (7 - c1));
+        row[k] = r0 > r1 ? 0u : (0x01010101u << (8 * r0)) & (0x01010101u >> (8 * (3 - r1)));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) m[k] = (col[k & 1] * row[k >> 1]) & s.Uk[k];
+}
+
+// Each lane offers one box (a frontier entry, a child, a point); the samples
+// any of them certainly covers are decided for the whole warp.
+__device__ __forceinline__ void certain_cover(Lane& s, int32_t x0, int32_t y0, int32_t x1, int32_t y1, int lane) {
+    if (s.q < 0) return;
+    uint32_t m[4];
+    certain_lanes(s, x0, y0, x1, y1, m);
+    if (!__any_sync(kFull, (m[0] | m[1] | m[2] | m[3]) != 0u)) return;
+    apply_cover(s, __reduce_or_sync(kFull, m[0]), __reduce_or_sync(kFull, m[1]), __reduce_or_sync(kFull, m[2]),
+                __reduce_or_sync(kFull, m[3]), lane);
+}
+
 // Lanes `cm` can reach and one of their undecided samples really is within
 // reach.  For the fill (R = 0, centres) the Chebyshev test is already exact.
 __device__ __forceinline__ bool reaches(const Lane& s, bool fill, uint32_t cm, int32_t x0, int32_t y0,
@@ -232,6 +272,7 @@ __device__ __forceinline__ bool reaches(const Lane& s, bool fill, uint32_t cm, i
 
 struct PointLeaf {
     static constexpr bool kFill = false;
+    static constexpr bool kCertain = true;   // boxes of points certainly cover nearby samples
     __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -241,6 +282,9 @@ struct PointLeaf {
         log_read(p, kLogLeaf, leaf, lane);
         int2 o = make_int2(kEmptyHi, kEmptyHi);
         if (i < src.n) o = __ldg((const int2*)src.obj + i);
+        // the square of half-side q around each point first, then the exact
+        // test on the samples still undecided in its reach
+        certain_cover(s, o.x, o.y, o.x, o.y, lane);
         uint32_t pm = rect_lanes(s, o.x, o.y, o.x, o.y) & s.U;
         if (!__any_sync(kFull, pm != 0)) return;
         const int32_t ps = 1 << s.L;
@@ -264,6 +308,7 @@ struct PointLeaf {
 
 struct SegLeaf {
     static constexpr bool kFill = false;
+    static constexpr bool kCertain = false;
     __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -304,6 +349,7 @@ struct SegLeaf {
 // unfilled pixel centre, count that polygon's own edges crossing the ray.
 struct FillLeaf {
     static constexpr bool kFill = true;
+    static constexpr bool kCertain = false;
     __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -361,12 +407,14 @@ struct FillLeaf {
 
 // Child boxes of one inner node: lane c computes the lanes child c can
 // reach, keeps it in `lm`, and the ballot selects the children to visit.
+// Point trees first decide the samples the children certainly cover.
 __device__ __forceinline__ uint32_t child_hits(const Params& p, bool fill, const Src& src,
-                                               const int32_t* base, const Lane& s, int lane, uint32_t* lm) {
+                                               const int32_t* base, Lane& s, int lane, uint32_t* lm) {
     if (p.log != nullptr)
         log_read(p, fill ? kLogPolyNode : kLogNode, (uint64_t)(base - src.nodes) >> 7, lane);
     int32_t x0 = __ldg(base + lane), y0 = __ldg(base + 32 + lane);
     int32_t x1 = __ldg(base + 64 + lane), y1 = __ldg(base + 96 + lane);
+    certain_cover(s, x0, y0, x1, y1, lane);
     uint32_t cm = rect_lanes(s, x0, y0, x1, y1);
     lm[lane] = cm;
     return __ballot_sync(kFull, reaches(s, fill, cm, x0, y0, x1, y1));
@@ -388,6 +436,7 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
     }
     uint32_t m0 = child_hits(p, V::kFill, src, src.lvl[lvl] + (uint64_t)node * 128, s, lane,
                              sm.lanemask[warp][lvl]);
+    if (s.U == 0) return;
     stk_node[lvl] = node;
     stk_mask[lvl] = m0;
     __syncwarp();
@@ -415,6 +464,7 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
             lvl--;
             uint32_t hm = child_hits(p, V::kFill, src, src.lvl[lvl] + (uint64_t)child * 128, s, lane,
                                      sm.lanemask[warp][lvl]);
+            if (s.U == 0) return;
             stk_node[lvl] = child;
             stk_mask[lvl] = hm;
             __syncwarp();
@@ -660,6 +710,15 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
     const int L = 23 - z;
     const int32_t ps = 1 << L;
     const int f_count = sm.f_count, f_level = sm.f_level, fb = sm.f_buf;
+    // certain-cover half-side: the largest q with 2 q^2 <= R^2
+    int32_t q = -1;
+    if (V::kCertain) {
+        const int64_t R2 = (int64_t)R * R;
+        int64_t t = (int64_t)((double)R * 0.70710678118654752);
+        while (t > 0 && 2 * t * t > R2) t--;
+        while (2 * (t + 1) * (t + 1) <= R2) t++;
+        q = (int32_t)t;
+    }
     while (true) {
         int blk = 0;
         if (lane == 0) blk = atomicAdd(&sm.next_block, 1);
@@ -686,6 +745,7 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
             s.nk = 4;
         }
         s.ext = (V::kFill ? 0 : R) + s.off;
+        s.q = q;
         s.U = kFull;
         for (int k = 0; k < 4; k++) s.Uk[k] = k < s.nk ? kFull : 0u;
         uint32_t und0 = s.und;
@@ -713,6 +773,7 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                         cm = rect_lanes(s, fbx.x, fbx.y, fbx.z, fbx.w);
                     }
                 }
+                certain_cover(s, fbx.x, fbx.y, fbx.z, fbx.w, lane);
                 uint32_t mm = __ballot_sync(kFull, reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
                 while (mm) {
                     int k = __ffs(mm) - 1;
