@@ -73,8 +73,26 @@ __device__ __forceinline__ bool segment_within(int32_t ax, int32_t ay, int32_t b
     return sq_le_prod(c, (uint64_t)R2, (uint64_t)L);
 }
 
+// The same test with the segment and the sample given relative to a nearby
+// origin: every endpoint within 2^30 of it and the sample within 2^27, so the
+// differences below fit 32 bits and each product is one 32 x 32 -> 64-bit
+// multiply.  d = b - a and L = d.d are passed in (fixed per segment).
+__device__ __forceinline__ bool segment_within_rel(int32_t ax, int32_t ay, int32_t bx, int32_t by, int32_t dx,
+                                                   int32_t dy, int64_t L, int32_t sx, int32_t sy, int64_t R2) {
+    const int32_t wx = sx - ax, wy = sy - ay;
+    const int64_t t = (int64_t)wx * dx + (int64_t)wy * dy;
+    if (t <= 0) return (int64_t)wx * wx + (int64_t)wy * wy <= R2;
+    if (t >= L) {
+        const int32_t ex = sx - bx, ey = sy - by;
+        return (int64_t)ex * ex + (int64_t)ey * ey <= R2;
+    }
+    const int64_t cr = (int64_t)wx * dy - (int64_t)wy * dx;
+    return sq_le_prod((uint64_t)(cr < 0 ? -cr : cr), (uint64_t)R2, (uint64_t)L);
+}
+
 // Edge (a, b) crosses the ray from c towards +x: half-open straddle in y,
-// crossing strictly right of c (Algorithm 2 ray casting).
+// crossing strictly right of c (Algorithm 2 ray casting).  All points lie in
+// the grid, so every difference fits 32 bits.
 __device__ __forceinline__ bool edge_crosses_right(int32_t ax, int32_t ay, int32_t bx, int32_t by,
                                                    int32_t cx, int32_t cy) {
     if ((ay > cy) == (by > cy)) return false;
@@ -82,7 +100,7 @@ __device__ __forceinline__ bool edge_crosses_right(int32_t ax, int32_t ay, int32
     if (ay > by) {
         lx = bx; ly = by; hx = ax; hy = ay;
     }
-    int64_t num = ((int64_t)hx - lx) * ((int64_t)cy - ly) - ((int64_t)cx - lx) * ((int64_t)hy - ly);
+    int64_t num = (int64_t)(hx - lx) * (cy - ly) - (int64_t)(cx - lx) * (hy - ly);
     return num > 0;
 }
 

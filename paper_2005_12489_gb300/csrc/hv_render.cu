@@ -199,20 +199,27 @@ __device__ __forceinline__ int64_t gap(int32_t a, int32_t b, int32_t v) {
 // stops at the first that qualifies.
 __device__ __forceinline__ bool round_reach(const Lane& s, int32_t x0, int32_t y0, int32_t x1,
                                             int32_t y1, uint32_t cand) {
-    const int32_t ps = 1 << s.L;
+    // box edges relative to the block's first pixel centre, clamped to
+    // +-2^30 (32-bit arithmetic below): a clamped edge lies more than
+    // 2^30 - 2^26 > R from every sample, so it never decides a gap within R
+    const int32_t ax = max(min(x0 - s.bx0, kGridHalf), -kGridHalf), bx = max(min(x1 - s.bx0, kGridHalf), -kGridHalf);
+    const int32_t ay = max(min(y0 - s.by0, kGridHalf), -kGridHalf), by = max(min(y1 - s.by0, kGridHalf), -kGridHalf);
     while (cand) {
         int l = __ffs(cand) - 1;
         cand &= cand - 1;
-        int32_t pcx = s.bx0 + (l & 7) * ps, pcy = s.by0 + (l >> 3) * ps;
-        int64_t dxm = gap(x0, x1, pcx - s.off), dxp = gap(x0, x1, pcx + s.off);
-        int64_t dym = gap(y0, y1, pcy - s.off), dyp = gap(y0, y1, pcy + s.off);
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (k < s.nk && ((s.Uk[k] >> l) & 1u)) {
-                int64_t dx = (k & 1) ? dxp : dxm, dy = (k & 2) ? dyp : dym;
-                if (dx * dx + dy * dy <= s.R2) return true;
-            }
-        }
+        const int32_t sx = (l & 7) << s.L, sy = (l >> 3) << s.L;
+        const uint32_t gxm = (uint32_t)max(max(ax - (sx - s.off), (sx - s.off) - bx), 0);
+        const uint32_t gxp = (uint32_t)max(max(ax - (sx + s.off), (sx + s.off) - bx), 0);
+        const uint32_t gym = (uint32_t)max(max(ay - (sy - s.off), (sy - s.off) - by), 0);
+        const uint32_t gyp = (uint32_t)max(max(ay - (sy + s.off), (sy + s.off) - by), 0);
+        const uint64_t xm = (uint64_t)gxm * gxm, xp = (uint64_t)gxp * gxp;
+        const uint64_t ym = (uint64_t)gym * gym, yp = (uint64_t)gyp * gyp;
+        const uint64_t R2 = (uint64_t)s.R2;
+        const bool h0 = (s.Uk[0] >> l) & 1u && xm + ym <= R2;
+        const bool h1 = (s.Uk[1] >> l) & 1u && xp + ym <= R2;
+        const bool h2 = (s.Uk[2] >> l) & 1u && xm + yp <= R2;
+        const bool h3 = (s.Uk[3] >> l) & 1u && xp + yp <= R2;
+        if (h0 | h1 | h2 | h3) return true;
     }
     return false;
 }
@@ -287,20 +294,37 @@ struct PointLeaf {
         certain_cover(s, o.x, o.y, o.x, o.y, lane);
         uint32_t pm = rect_lanes(s, o.x, o.y, o.x, o.y) & s.U;
         if (!__any_sync(kFull, pm != 0)) return;
-        const int32_t ps = 1 << s.L;
+        // the point relative to the block's first pixel centre; lanes in pm
+        // are within reach, so the 32-bit differences below are exact
+        const int32_t dxo = max(min(o.x - s.bx0, kGridHalf), -kGridHalf);
+        const int32_t dyo = max(min(o.y - s.by0, kGridHalf), -kGridHalf);
+        const uint64_t R2 = (uint64_t)s.R2;
         uint32_t c[4] = {0u, 0u, 0u, 0u};
-        while (pm) {
-            int l = __ffs(pm) - 1;
-            pm &= pm - 1;
-            int32_t pcx = s.bx0 + (l & 7) * ps, pcy = s.by0 + (l >> 3) * ps;
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if (k < s.nk && ((s.Uk[k] >> l) & 1u) &&
-                    point_within(o.x, o.y, pcx + ((k & 1) ? s.off : -s.off), pcy + ((k & 2) ? s.off : -s.off),
-                                 s.R2))
-                    c[k] |= 1u << l;
+        if (s.nk == 1) {
+            while (pm) {
+                int l = __ffs(pm) - 1;
+                pm &= pm - 1;
+                const int32_t dx = dxo - ((l & 7) << s.L), dy = dyo - ((l >> 3) << s.L);
+                if ((uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) <= R2) c[0] |= 1u << l;
+            }
+        } else {
+            while (pm) {
+                int l = __ffs(pm) - 1;
+                pm &= pm - 1;
+                // point minus sample: sample k sits at -+off in x (bit 0) and y (bit 1)
+                const int32_t dx = dxo - ((l & 7) << s.L), dy = dyo - ((l >> 3) << s.L);
+                const uint64_t xm = (uint64_t)((int64_t)(dx + s.off) * (dx + s.off));
+                const uint64_t xp = (uint64_t)((int64_t)(dx - s.off) * (dx - s.off));
+                const uint64_t ym = (uint64_t)((int64_t)(dy + s.off) * (dy + s.off));
+                const uint64_t yp = (uint64_t)((int64_t)(dy - s.off) * (dy - s.off));
+                const uint32_t bit = 1u << l;
+                if (xm + ym <= R2) c[0] |= bit;
+                if (xp + ym <= R2) c[1] |= bit;
+                if (xm + yp <= R2) c[2] |= bit;
+                if (xp + yp <= R2) c[3] |= bit;
             }
         }
+        // decided samples may be hit again: apply_cover only clears bits
         apply_cover(s, __reduce_or_sync(kFull, c[0]), __reduce_or_sync(kFull, c[1]),
                     __reduce_or_sync(kFull, c[2]), __reduce_or_sync(kFull, c[3]), lane);
     }
@@ -317,7 +341,7 @@ struct SegLeaf {
         uint64_t i = (uint64_t)leaf * 32 + lane;
         log_read(p, kLogLeaf, leaf, lane);
         // a record is a piece: the whole segment and the box of its piece
-        int4 o = make_int4(kEmptyHi, kEmptyHi, kEmptyHi, kEmptyHi);
+        int4 o = make_int4(0, 0, 0, 0);   // padding: never in reach (empty piece box)
         int4 pb = make_int4(kEmptyLo, kEmptyLo, kEmptyHi, kEmptyHi);
         if (i < src.n) {
             o = __ldg((const int4*)src.obj + 2 * i);
@@ -326,18 +350,26 @@ struct SegLeaf {
         const int32_t sx0 = pb.x, sy0 = pb.y, sx1 = pb.z, sy1 = pb.w;
         uint32_t pm = rect_lanes(s, sx0, sy0, sx1, sy1) & s.U;
         if (!__any_sync(kFull, pm != 0)) return;
-        const int32_t ps = 1 << s.L;
+        // the segment relative to the block's first pixel centre (differences
+        // of grid points fit 32 bits); 32-bit arithmetic when both endpoints
+        // are within 2^30 of it, else the absolute 64-bit test
+        const int32_t ax = o.x - s.bx0, ay = o.y - s.by0, bx = o.z - s.bx0, by = o.w - s.by0;
+        const bool near = max(max(abs(ax), abs(ay)), max(abs(bx), abs(by))) <= kGridHalf;
+        const int32_t dx = o.z - o.x, dy = o.w - o.y;
+        const int64_t Ls = (int64_t)dx * dx + (int64_t)dy * dy;
         uint32_t c[4] = {0u, 0u, 0u, 0u};
         while (pm) {
             int l = __ffs(pm) - 1;
             pm &= pm - 1;
-            int32_t pcx = s.bx0 + (l & 7) * ps, pcy = s.by0 + (l >> 3) * ps;
+            const int32_t px = (l & 7) << s.L, py = (l >> 3) << s.L;
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                if (k < s.nk && ((s.Uk[k] >> l) & 1u) &&
-                    segment_within(o.x, o.y, o.z, o.w, pcx + ((k & 1) ? s.off : -s.off),
-                                   pcy + ((k & 2) ? s.off : -s.off), s.R2))
-                    c[k] |= 1u << l;
+                if (k < s.nk && ((s.Uk[k] >> l) & 1u)) {
+                    const int32_t sx = px + ((k & 1) ? s.off : -s.off), sy = py + ((k & 2) ? s.off : -s.off);
+                    const bool hit = near ? segment_within_rel(ax, ay, bx, by, dx, dy, Ls, sx, sy, s.R2)
+                                          : segment_within(o.x, o.y, o.z, o.w, s.bx0 + sx, s.by0 + sy, s.R2);
+                    if (hit) c[k] |= 1u << l;
+                }
             }
         }
         apply_cover(s, __reduce_or_sync(kFull, c[0]), __reduce_or_sync(kFull, c[1]),
