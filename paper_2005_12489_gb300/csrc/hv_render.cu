@@ -289,9 +289,7 @@ struct PointLeaf {
         log_read(p, kLogLeaf, leaf, lane);
         int2 o = make_int2(kEmptyHi, kEmptyHi);
         if (i < src.n) o = __ldg((const int2*)src.obj + i);
-        // the square of half-side q around each point first, then the exact
-        // test on the samples still undecided in its reach
-        certain_cover(s, o.x, o.y, o.x, o.y, lane);
+        // the exact test on the undecided samples in each point's reach
         uint32_t pm = rect_lanes(s, o.x, o.y, o.x, o.y) & s.U;
         if (!__any_sync(kFull, pm != 0)) return;
         // the point relative to the block's first pixel centre; lanes in pm
@@ -868,7 +866,15 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
+// CTAs per SM: points keep four (their traversal fits 64 registers); the
+// segment and fill paths run faster with the registers of three.
+template <int kKind>
+struct KindTraits {
+    static constexpr int kBlocksPerSM = kKind == HV_LAYER_POINTS ? 4 : 3;
+};
+
+template <int kKind>
+__global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_render(const Params p) {
     __shared__ Smem sm;
     const int tid = threadIdx.x;
     const int rows = p.rows;
@@ -897,14 +903,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_render(const Params p) {
         const int32_t sy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1) + off;
         const bool learned = p.use_learned != 0;
         // Algorithm 1 over points / segments / polygon edges
-        if (p.kind == HV_LAYER_POINTS)
+        if constexpr (kKind == HV_LAYER_POINTS)
             stage<PointLeaf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
                              p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
         else
             stage<SegLeaf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
                            p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
         // Algorithm 2 over polygon boxes and edges
-        if (p.kind == HV_LAYER_POLYGONS) {
+        if constexpr (kKind == HV_LAYER_POLYGONS) {
             const int32_t cx0 = X0 + (ps >> 1), cx1 = X0 + (kTile - 1) * ps + (ps >> 1);
             const int32_t cy0 = Y0 + strip * rows * ps + (ps >> 1);
             const int32_t cy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1);
@@ -1046,7 +1052,9 @@ int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint64_t resident = (uint64_t)sms * 4;
+    const int per_sm = L->kind == HV_LAYER_POINTS ? KindTraits<HV_LAYER_POINTS>::kBlocksPerSM
+                                                  : KindTraits<HV_LAYER_LINES>::kBlocksPerSM;
+    const uint64_t resident = (uint64_t)sms * per_sm;
     p.rows = (uint64_t)n * 16 >= 2 * resident ? 16 : ((uint64_t)n * 32 >= 2 * resident ? 8 : 4);
     p.strips = kTile / p.rows;
     uint64_t grid = (uint64_t)n * p.strips;
@@ -1054,7 +1062,12 @@ int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int
         set_error("too many tiles in one call");
         return HV_EINVAL;
     }
-    k_render<<<(unsigned)grid, kThreads, 0, stream>>>(p);
+    if (L->kind == HV_LAYER_POINTS)
+        k_render<HV_LAYER_POINTS><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+    else if (L->kind == HV_LAYER_LINES)
+        k_render<HV_LAYER_LINES><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+    else
+        k_render<HV_LAYER_POLYGONS><<<(unsigned)grid, kThreads, 0, stream>>>(p);
     HV_CUDA(cudaGetLastError());
     return HV_OK;
 }
