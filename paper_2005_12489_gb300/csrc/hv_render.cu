@@ -272,6 +272,78 @@ __device__ __forceinline__ bool reaches(const Lane& s, bool fill, uint32_t cm, i
     return fill || round_reach(s, x0, y0, x1, y1, cand);
 }
 
+// Pixels of the block whose centre lies within E of the segment's line,
+// E = R + 2 off + slack >= R + off * sqrt 2 (a covered sample's pixel centre
+// is that close): in pixel row r the centres (c ps, r ps), relative to the
+// block's first centre, satisfy |c A + K_r| <= B with A = ps dy,
+// K_r = cross((0, r ps) - P, d), B = E |d|, P a point within 2 units of the
+// line (the centre of the piece box: a piece runs corner to corner of it).
+// Single precision with every bound widened by more than its rounding error
+// (relative 2^-20 of the magnitudes involved, plus a column): a superset of
+// the pixels the exact test can cover.
+__device__ __forceinline__ uint32_t line_lanes(const Lane& s, int32_t px, int32_t py, int32_t dx, int32_t dy) {
+    const float fdx = (float)dx, fdy = (float)dy, fpx = (float)px, fpy = (float)py;
+    const float dn = sqrtf(fmaf(fdx, fdx, fdy * fdy));
+    const float E = (float)(s.ext + s.off + 2) + (fabsf(fpx) + fabsf(fpy)) * 0x1p-22f;
+    const float B = E * dn * (1.0f + 0x1p-20f);
+    const float ps = (float)(1 << s.L);
+    const float A = ps * fdy;
+    const float inv = A != 0.f ? 1.0f / A : 0.f;
+    uint32_t m = 0u;
+#pragma unroll
+    for (int r = 0; r < kBH; r++) {
+        const float t1 = -fpx * fdy, t2 = fmaf((float)r, ps, -fpy) * fdx;
+        const float K = t1 - t2;
+        const float mag = fabsf(t1) + fabsf(t2) + B;
+        uint32_t row;
+        if (A == 0.f) {
+            row = fabsf(K) <= B + mag * 0x1p-20f ? 0xFFu : 0u;
+        } else {
+            float lo = (-B - K) * inv, hi = (B - K) * inv;
+            if (inv < 0.f) {
+                const float t = lo;
+                lo = hi;
+                hi = t;
+            }
+            const float err = fmaf(mag * fabsf(inv), 0x1p-20f, 1.0f) + (fabsf(lo) + fabsf(hi)) * 0x1p-20f;
+            lo = fmaxf(lo - err, -1.f);
+            hi = fminf(hi + err, 8.f);
+            const int c0 = max((int)ceilf(lo), 0), c1 = min((int)floorf(hi), 7);
+            row = c0 <= c1 ? (0xFFu << c0) & (0xFFu >> (7 - c1)) : 0u;
+        }
+        m |= row << (8 * r);
+    }
+    return m;
+}
+
+// Pixels of the block whose centre the edge e crosses strictly to the right
+// (Algorithm 2's ray test, half-open straddle in y): per pixel row the
+// orientation num(c) = dx (y - ly) - (x_c - lx) dy of the edge ordered by y
+// falls as the column c grows, so the crossed columns are a prefix 0..t-1,
+// t found by a three-step binary search with exact 64-bit products.
+__device__ __forceinline__ uint32_t crossing_columns(int4 e, const Lane& s) {
+    int32_t lx = e.x, ly = e.y, hx = e.z, hy = e.w;
+    if (ly > hy) {
+        lx = e.z; ly = e.w; hx = e.x; hy = e.y;
+    }
+    if (ly == hy) return 0u;   // a level edge straddles no scanline
+    const int32_t ex = hx - lx, ey = hy - ly;
+    uint32_t m = 0u;
+#pragma unroll
+    for (int r = 0; r < kBH; r++) {
+        const int32_t y = s.by0 + (r << s.L);
+        if (y < ly || y >= hy) continue;
+        const int64_t n0 = (int64_t)ex * (y - ly) - (int64_t)(s.bx0 - lx) * ey;
+        // column c is crossed iff n0 > c ps ey
+        int t = n0 > (int64_t)(3 << s.L) * ey ? 4 : 0;
+        if (n0 > (int64_t)((t + 1) << s.L) * ey) t += 2;
+        if (n0 > (int64_t)(t << s.L) * ey) t += 1;
+        if (t == 7 && n0 > (int64_t)(7 << s.L) * ey) t = 8;
+        m |= ((1u << t) - 1u) << (8 * r);
+    }
+    return m;
+}
+
 // ---- leaf visitors -----------------------------------------------------------
 // Points and segments: each lane takes one object of the leaf and evaluates
 // the exact predicate on the undecided samples within its reach; the
@@ -348,6 +420,9 @@ struct SegLeaf {
         const int32_t sx0 = pb.x, sy0 = pb.y, sx1 = pb.z, sy1 = pb.w;
         uint32_t pm = rect_lanes(s, sx0, sy0, sx1, sy1) & s.U;
         if (!__any_sync(kFull, pm != 0)) return;
+        // a piece box much larger than the pixels: keep the pixels near the line
+        if (__reduce_max_sync(kFull, (uint32_t)__popc(pm)) > 8u)
+            pm &= line_lanes(s, mid32(sx0, sx1) - s.bx0, mid32(sy0, sy1) - s.by0, o.z - o.x, o.w - o.y);
         // the segment relative to the block's first pixel centre (differences
         // of grid points fit 32 bits); 32-bit arithmetic when both endpoints
         // are within 2^30 of it, else the absolute 64-bit test
@@ -413,17 +488,15 @@ struct FillLeaf {
                 if (lane == 0) check_failed(p, 6, ((uint64_t)pid << 24) | (e1 & 0xffffff));
                 continue;
             }
-            uint32_t parity = 0;
+            // each lane takes an edge; the crossed pixels of all the edges,
+            // XOR-reduced, are every pixel's parity at once
+            uint32_t par = 0u;
             for (uint64_t base = e0; base < e1; base += 32) {
-                int4 e = make_int4(0, 0, 0, 0);
-                if (base + lane < e1) e = __ldg(p.poly_edges + base + lane);
-                int cnt = (e1 - base) < 32 ? (int)(e1 - base) : 32;
-                for (int j = 0; j < cnt; j++) {
-                    int32_t ax = __shfl_sync(kFull, e.x, j), ay = __shfl_sync(kFull, e.y, j);
-                    int32_t cx2 = __shfl_sync(kFull, e.z, j), cy2 = __shfl_sync(kFull, e.w, j);
-                    if (active && edge_crosses_right(ax, ay, cx2, cy2, s.cx, s.cy)) parity ^= 1u;
-                }
+                uint32_t cm = 0u;
+                if (base + lane < e1) cm = crossing_columns(__ldg(p.poly_edges + base + lane), s);
+                par ^= __reduce_xor_sync(kFull, cm);
             }
+            const uint32_t parity = (par >> lane) & 1u;
             if (active && parity) s.und = 0;
             uint32_t U2 = __ballot_sync(kFull, s.und != 0);
             if (U2 != s.U) {
