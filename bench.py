@@ -72,6 +72,9 @@ def parse():
                     help="index timed for the headline value (both are reported)")
     ap.add_argument("--profile-steps", action="store_true",
                     help="only warm-up + steps, no baselines (for ncu launch lists)")
+    ap.add_argument("--volume-sweep", default=None,
+                    help="comma-separated point counts: the clustered-points tiles rendered over layers of "
+                         "each size (the same 10,000 tiles), one JSON line")
     return ap.parse_args()
 
 
@@ -139,6 +142,36 @@ def measured_peak_hbm():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+KERNEL_SOURCES = ("hv_render.cu", "hv_device.cuh", "hv_learned.cuh", "hv_internal.h")
+PROFILES = {2: "k_render_points_gmm100M.md", 3: "k_render_lines_walk50M.md", 4: "k_render_polygons_star2M.md"}
+
+
+def kernel_source_hash():
+    """sha256 over the sources the render kernel is compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2005_12489_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(cfg):
+    """DRAM bytes (read + write) of one full-size launch of the render kernel,
+    from the committed ncu summary, if the kernel sources still hash to the
+    value recorded beside it; else None."""
+    path = os.path.join(ROOT, "profiles", PROFILES.get(cfg, ""))
+    if not os.path.isfile(path):
+        return None
+    want = kernel_source_hash()
+    for ln in open(path):
+        if ln.startswith("traffic_per_launch_bytes:"):
+            parts = ln.split()
+            if len(parts) >= 4 and parts[2] == "kernel_sources_sha256" and parts[3] == want:
+                return int(parts[1])
+    return None
 
 
 class Layer:
@@ -290,9 +323,12 @@ def algorithmic_bytes_per_tile(hv, layer, reqs_dev_np, torch, n_sample, lay):
         read += int(lay.poly_edges[pid].sum()) * 16 + 16 * len(pid)
     k = len(sample)
     per_tile = read / k + hv.hv_tile_bytes(hv.HV_MODE_RGBA) + 16
-    return {"per_tile": per_tile, "read_per_tile": read / k, "unique_nodes_per_tile": nodes / k,
-            "unique_leaves_per_tile": leaves / k, "node_visits_per_tile": int((vkind == 0).sum()) / k,
-            "leaf_visits_per_tile": int((vkind == 1).sum()) / k, "sample_tiles": k}
+    node_visits = int(((vkind == 0) | (vkind == 2)).sum()) / k
+    leaf_visits = int(((vkind == 1) | (vkind == 3)).sum()) / k
+    return {"per_tile": per_tile, "read_per_tile": read / k, "unique_nodes_per_tile": (nodes + pnodes) / k,
+            "unique_leaves_per_tile": (leaves + pleaves) / k, "node_visits_per_tile": node_visits,
+            "leaf_visits_per_tile": leaf_visits, "node_visits_per_pixel": node_visits / 65536,
+            "leaf_visits_per_pixel": leaf_visits / 65536, "sample_tiles": k}
 
 
 def run_gb300(args):
@@ -415,7 +451,7 @@ def run_gb300(args):
         if alg is not None:
             achieved = alg["per_tile"] * n / (ms / 1000.0) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                    "frac": achieved / peak, "traffic": measured_traffic(args.config), "peak_kind": peak_kind,
                     "kernel": "k_render", "alg_bytes_per_tile": alg["per_tile"],
                     "alg_detail": alg}
         e2e = None
@@ -526,12 +562,74 @@ def run_serving(args):
     hv.hv_destroy(ctx)
 
 
+def run_volume_sweep(args):
+    """The clustered-points workload's 10,000 tiles (drawn from the 100M-point
+    layer) rendered over layers of N points from the same mixture, for each N:
+    tiles/s, index build time and the traversal's visits per tile (the paper's
+    claim that display-driven rendering time hardly depends on data volume,
+    Sec. 5.3)."""
+    import torch
+    from paper_2005_12489_gb300 import hv
+    sizes = [int(v) for v in args.volume_sweep.split(",")]
+    w = WORKLOADS[2]
+    ref_pts = gen.gmm_points(w["n_objects"], seed=2, k=64)
+    reqs = gen.density_tiles(ref_pts, args.tiles, w["zoom"][0], w["zoom"][1], w["r16"], seed=102)
+    del ref_pts
+    ctx = hv.hv_create(0)
+    mode = hv.HV_MODE_RGBA
+    tb = hv.hv_tile_bytes(mode)
+    n = len(reqs)
+    style = hv.make_style(STYLE_T[:3], STYLE_T[4:7])
+    d_req = torch.from_numpy(hv.make_requests(reqs).view(np.uint8).copy()).cuda()
+    d_out = torch.empty((n, tb), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    for size in sizes:
+        pts = gen.gmm_points(size, seed=2, k=64)
+        layer = hv.hv_layer_load_points(ctx, pts)
+        del pts
+        hv.hv_layer_build_index(layer, hv.HV_INDEX_RTREE)
+        info = hv.hv_layer_info_get(layer)
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            hv.hv_render_tiles(layer, d_req, n, mode, hv.HV_INDEX_RTREE, style, d_out, d_out.numel(), stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(k & 255)
+            evs[k][0].record(stream)
+            hv.hv_render_tiles(layer, d_req, n, mode, hv.HV_INDEX_RTREE, style, d_out, d_out.numel(), stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+
+        class _L:
+            kind, obj_bytes, n_objects = "points", 8, size
+        alg = algorithmic_bytes_per_tile(hv, layer, reqs, torch, args.count_sample_tiles, _L)
+        rows.append({"points": size, "tiles_per_s": n / (ms / 1000.0), "ms_per_step": ms,
+                     "index_build_ms": info.build_ms, "tree_levels": info.tree_levels,
+                     "node_visits_per_tile": alg and alg["node_visits_per_tile"],
+                     "leaf_visits_per_tile": alg and alg["leaf_visits_per_tile"],
+                     "unique_bytes_read_per_tile": alg and alg["read_per_tile"]})
+        hv.hv_layer_free(layer)
+    hv.hv_destroy(ctx)
+    print(json.dumps({"metric": "tiles/s vs data volume (same tiles)", "unit": "tiles/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                      "data": "synthetic", "dtype": "int64",
+                      "config": {"workload": w["workload"].replace("clustered points 100M", "clustered points N"),
+                                 "tiles_from": "the 100M-point layer (seed 2)"},
+                      "sweep": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.config == 5:
         run_serving(args)
+    elif args.volume_sweep:
+        run_volume_sweep(args)
     else:
         run_gb300(args)
 
