@@ -573,7 +573,7 @@ def run_volume_sweep(args):
     layer) rendered over layers of N points from the same mixture, for each N:
     tiles/s, index build time and the traversal's visits per tile (the paper's
     claim that display-driven rendering time hardly depends on data volume,
-    Sec. 5.3)."""
+    Sec. 3.3 and Exp. 1)."""
     import torch
     from paper_2005_12489_gb300 import hv
     sizes = [int(v) for v in args.volume_sweep.split(",")]
