@@ -181,6 +181,16 @@ typedef void (*splat_fn)(const void* obj, uint32_t z, int64_t X0, int64_t Y0,
 
 /* Visit every requested tile whose area lies within the largest requested
  * radius of the box [x0, x1] x [y0, y1] and call f on it. */
+/* Call f on request i (tile (z, tx, ty)) with the tile's origin and radius. */
+static void call_request(const req_table* t, uint64_t i, uint32_t z, int64_t tx, int64_t ty,
+                         const void* obj, splat_fn f) {
+    int64_t span = (int64_t)1 << (31 - z);
+    uint32_t r = t->refs[i].req;
+    int64_t R = radius_units(t->r16[r], z);
+    f(obj, z, -GRID_HALF + tx * span, -GRID_HALF + ty * span, R,
+      t->flags + (uint64_t)r * TILE_PX * TILE_PX);
+}
+
 static void for_each_request(const req_table* t, int64_t x0, int64_t y0, int64_t x1,
                              int64_t y1, const void* obj, splat_fn f) {
     for (uint32_t z = 0; z < 32; z++) {
@@ -190,16 +200,22 @@ static void for_each_request(const req_table* t, int64_t x0, int64_t y0, int64_t
         if (x0 - E >= GRID_HALF || y0 - E >= GRID_HALF) continue;
         int64_t tx0 = tile_of(x0 - E, z), tx1 = tile_of(x1 + E, z);
         int64_t ty0 = tile_of(y0 - E, z), ty1 = tile_of(y1 + E, z);
-        int64_t span = (int64_t)1 << (31 - z);
+        uint64_t lo = table_lower(t, tile_key(z, 0, 0)), hi = table_lower(t, tile_key(z + 1, 0, 0));
+        if ((uint64_t)(tx1 - tx0 + 1) * (uint64_t)(ty1 - ty0 + 1) > hi - lo) {
+            /* the box spans more tiles than were requested at this zoom: the
+               same calls, found by scanning this zoom's requests instead */
+            for (uint64_t i = lo; i < hi; i++) {
+                int64_t tx = (int64_t)((t->refs[i].key >> 24) & 0xFFFFFF), ty = (int64_t)(t->refs[i].key & 0xFFFFFF);
+                if (tx < tx0 || tx > tx1 || ty < ty0 || ty > ty1) continue;
+                call_request(t, i, z, tx, ty, obj, f);
+            }
+            continue;
+        }
         for (int64_t tx = tx0; tx <= tx1; tx++) {
             for (int64_t ty = ty0; ty <= ty1; ty++) {
                 uint64_t k = tile_key(z, (uint32_t)tx, (uint32_t)ty);
-                for (uint64_t i = table_lower(t, k); i < t->n && t->refs[i].key == k; i++) {
-                    uint32_t r = t->refs[i].req;
-                    int64_t R = radius_units(t->r16[r], z);
-                    f(obj, z, -GRID_HALF + tx * span, -GRID_HALF + ty * span, R,
-                      t->flags + (uint64_t)r * TILE_PX * TILE_PX);
-                }
+                for (uint64_t i = table_lower(t, k); i < t->n && t->refs[i].key == k; i++)
+                    call_request(t, i, z, tx, ty, obj, f);
             }
         }
     }
