@@ -42,6 +42,7 @@ WORKLOADS = {
 WORKLOAD = WORKLOADS[2]
 METRIC = "tiles/sec (256² px) and p99 tile latency, learned vs R-tree index, 1 GB300"
 STYLE_T = (230, 40, 20, 0, 30, 90, 200, 0)
+NOUN = {"points": "points", "lines": "segments", "polygons": "polygons"}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -264,7 +265,8 @@ def cpu_rtree_baseline(lay, n_sample):
     tree.close()
     return {"value": n_sample / dt, "unit": "tiles/s", "cores": threads,
             "kind": "cpu packed R-tree, per-sample queries",
-            "sample": "%d of the %d tiles (evenly spaced), all %d %s" % (n_sample, len(lay.reqs), lay.n_objects, lay.kind),
+            "sample": "%d of the %d tiles (evenly spaced), all %d %s" % (n_sample, len(lay.reqs), lay.n_objects,
+                                                                        NOUN[lay.kind]),
             "build_s": build_s, "seconds": dt}
 
 

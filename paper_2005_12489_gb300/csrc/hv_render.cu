@@ -35,6 +35,7 @@ constexpr int kBW = 8, kBH = 4;
 constexpr int kBlocksX = kTile / kBW;
 constexpr int kFCap = 512;
 constexpr int kBucketCap = 2048;   // keeps the static shared memory under 48 KiB
+constexpr int kCullCells = 64;     // learned cull: at most this many Hilbert cells per strip
 
 // result bits per pixel
 constexpr uint32_t kResCentre = 16u, kResFill = 32u;
@@ -686,7 +687,7 @@ __device__ void learned_cull(const Params& p, const TreeArg& t, const LModel& m,
     while (k < 31) {
         int64_t nx = ((x1 + kGridHalf) >> k) - ((x0 + kGridHalf) >> k) + 1;
         int64_t ny = ((y1 + kGridHalf) >> k) - ((y0 + kGridHalf) >> k) + 1;
-        if (nx * ny <= kThreads) break;
+        if (nx * ny <= kCullCells) break;
         k++;
     }
     const int64_t gx0 = (x0 + kGridHalf) >> k, gy0 = (y0 + kGridHalf) >> k;

@@ -179,6 +179,54 @@ def test_grid_extremes(ctx):
     check_points(ctx, p, np.array(reqs, dtype=np.uint32))
 
 
+def _tiles_along(segs, zooms, per_seg, rng, r16s):
+    """Tiles that contain sampled points of the given segments (x0, y0, x1, y1)."""
+    half = 1 << 30
+    out = []
+    for (x0, y0, x1, y1) in segs:
+        for t in rng.uniform(0.0, 1.0, per_seg):
+            x = int(x0 + (x1 - x0) * t)
+            y = int(y0 + (y1 - y0) * t)
+            z = int(rng.choice(zooms))
+            out.append([z, (x + half) >> (31 - z), (y + half) >> (31 - z), int(rng.choice(r16s))])
+    return np.array(out, dtype=np.uint32)
+
+
+def test_grid_spanning_segments(ctx):
+    """Segments across the whole grid seen at high zoom: endpoints far from
+    every pixel block (the absolute 64-bit test), pieces far larger than the
+    pixels (the band filter), slopes near 0, 1 and infinity."""
+    half = 1 << 30
+    segs = [(-half, -half, half - 1, half - 1), (-half, 12345, half - 1, 12346),
+            (777, -half, 778, half - 1), (-half + 5, half - 9, half - 3, -half + 1),
+            (-(1 << 29), 3, (1 << 29) + 17, 1 << 20), (100, 200, 100 + (1 << 27), 200 + (1 << 13))]
+    xy = np.array([[a, b] for s in segs for a, b in ((s[0], s[1]), (s[2], s[3]))], dtype=np.int32)
+    off = np.arange(0, 2 * len(segs) + 1, 2, dtype=np.uint64)
+    rng = np.random.default_rng(21)
+    reqs = np.concatenate([_tiles_along(segs, [0, 3, 9, 14, 17, 19], 6, rng, [1, 8, 16, 100]),
+                           np.array([[0, 0, 0, 1024], [2, 1, 2, 64]], dtype=np.uint32)])
+    check_lines(ctx, xy, off, reqs)
+
+
+def test_grid_spanning_polygon_edges(ctx):
+    """A polygon over most of the grid, a thin sliver and a square hole: the
+    fill's per-row crossing counts with edges far from the block, at high zoom
+    along the edges and inside."""
+    half = 1 << 30
+    big = [(-half, -half), (half - 1, -half + 7), (3, half - 1)]
+    sliver = [(-half + 10, 5), (half - 10, 7), (half - 10, 9), (-half + 10, 6)]
+    hole = [(-1000000, -1000000), (-1000000, 1000000), (1000000, 1000000), (1000000, -1000000)]
+    xy = np.array(big + hole + sliver, dtype=np.int32)
+    ro = np.array([0, 3, 7, 11], dtype=np.uint64)
+    po = np.array([0, 2, 3], dtype=np.uint64)
+    edges = [big[i] + big[(i + 1) % 3] for i in range(3)] + [sliver[i] + sliver[(i + 1) % 4] for i in range(4)]
+    rng = np.random.default_rng(22)
+    reqs = np.concatenate([_tiles_along(edges, [1, 6, 12, 16, 19], 4, rng, [1, 8, 40]),
+                           np.array([[19, 1 << 18, 1 << 18, 8], [12, 2047, 2047, 8], [0, 0, 0, 16]],
+                                    dtype=np.uint32)])
+    check_polygons(ctx, xy, ro, po, reqs)
+
+
 def test_empty_and_single_object_layers(ctx):
     reqs = np.array([[0, 0, 0, 16], [7, 64, 64, 40]], dtype=np.uint32)
     check_points(ctx, np.zeros((0, 2), np.int32), reqs)
