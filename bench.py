@@ -242,7 +242,7 @@ def cpu_baseline(lay, n_sample):
     dt = time.perf_counter() - t0
     return {"value": n_sample / dt, "unit": "tiles/s", "cores": 1, "kind": "oracle",
             "sample": "%d of the %d tiles (evenly spaced), all %d %s, single-threaded C"
-                      % (n_sample, len(reqs), lay.n_objects, lay.kind), "seconds": dt}
+                      % (n_sample, len(reqs), lay.n_objects, NOUN[lay.kind]), "seconds": dt}
 
 
 def cpu_rtree_baseline(lay, n_sample):
@@ -294,7 +294,7 @@ def run_reference(args):
             "config": dict(WORKLOADS[args.config], sample_tiles_per_step=n_sample),
             "cpu_baseline": {"value": value, "unit": "tiles/s", "cores": 1, "kind": "oracle",
                              "sample": "%d tiles per step of the %d-tile batch, all %d %s"
-                                       % (n_sample, len(reqs), lay.n_objects, lay.kind)},
+                                       % (n_sample, len(reqs), lay.n_objects, NOUN[lay.kind])},
             "e2e": {"value": value, "unit": "tiles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
