@@ -76,9 +76,13 @@ __device__ __forceinline__ bool segment_within(int32_t ax, int32_t ay, int32_t b
 // The same test with the segment and the sample given relative to a nearby
 // origin: every endpoint within 2^30 of it and the sample within 2^27, so the
 // differences below fit 32 bits and each product is one 32 x 32 -> 64-bit
-// multiply.  d = b - a and L = d.d are passed in (fixed per segment).
+// multiply.  d = b - a and L = d.d are passed in (fixed per segment), and so
+// are bounds c_lo <= R |d| <= c_hi (c_lo = -1, c_hi = INT64_MAX when unknown):
+// |cross| <= c_lo means (w x d)^2 < R^2 L, |cross| > c_hi the opposite, and
+// only a cross product between them needs the 128-bit comparison.
 __device__ __forceinline__ bool segment_within_rel(int32_t ax, int32_t ay, int32_t bx, int32_t by, int32_t dx,
-                                                   int32_t dy, int64_t L, int32_t sx, int32_t sy, int64_t R2) {
+                                                   int32_t dy, int64_t L, int64_t c_lo, int64_t c_hi, int32_t sx,
+                                                   int32_t sy, int64_t R2) {
     const int32_t wx = sx - ax, wy = sy - ay;
     const int64_t t = (int64_t)wx * dx + (int64_t)wy * dy;
     if (t <= 0) return (int64_t)wx * wx + (int64_t)wy * wy <= R2;
@@ -87,7 +91,10 @@ __device__ __forceinline__ bool segment_within_rel(int32_t ax, int32_t ay, int32
         return (int64_t)ex * ex + (int64_t)ey * ey <= R2;
     }
     const int64_t cr = (int64_t)wx * dy - (int64_t)wy * dx;
-    return sq_le_prod((uint64_t)(cr < 0 ? -cr : cr), (uint64_t)R2, (uint64_t)L);
+    const int64_t c = cr < 0 ? -cr : cr;
+    if (c <= c_lo) return true;
+    if (c > c_hi) return false;
+    return sq_le_prod((uint64_t)c, (uint64_t)R2, (uint64_t)L);
 }
 
 // Edge (a, b) crosses the ray from c towards +x: half-open straddle in y,

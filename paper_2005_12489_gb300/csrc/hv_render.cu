@@ -188,13 +188,6 @@ __device__ __forceinline__ uint32_t rect_lanes(const Lane& s, int32_t x0, int32_
     return col * rows;
 }
 
-// Distance from v to the interval [a, b] (0 inside).
-__device__ __forceinline__ int64_t gap(int32_t a, int32_t b, int32_t v) {
-    int64_t d1 = (int64_t)a - v, d2 = (int64_t)v - b;
-    int64_t d = d1 > d2 ? d1 : d2;
-    return d > 0 ? d : 0;
-}
-
 // Does the box [x0, x1] x [y0, y1] come within Euclidean distance R of an
 // undecided sample of one of the lanes in `cand`?  Exact for every sample;
 // stops at the first that qualifies.
@@ -253,7 +246,7 @@ __device__ __forceinline__ void certain_lanes(const Lane& s, int32_t x0, int32_t
     for (int k = 0; k < 4; k++) m[k] = (col[k & 1] * row[k >> 1]) & s.Uk[k];
 }
 
-// Each lane offers one box (a frontier entry, a child, a point); the samples
+// Each lane offers one box (a child of the node being visited); the samples
 // any of them certainly covers are decided for the whole warp.
 __device__ __forceinline__ void certain_cover(Lane& s, int32_t x0, int32_t y0, int32_t x1, int32_t y1, int lane) {
     if (s.q < 0) return;
@@ -401,6 +394,7 @@ struct PointLeaf {
     }
 };
 
+template <bool kScreen>
 struct SegLeaf {
     static constexpr bool kFill = false;
     static constexpr bool kCertain = false;
@@ -431,6 +425,16 @@ struct SegLeaf {
         const bool near = max(max(abs(ax), abs(ay)), max(abs(bx), abs(by))) <= kGridHalf;
         const int32_t dx = o.z - o.x, dy = o.w - o.y;
         const int64_t Ls = (int64_t)dx * dx + (int64_t)dy * dy;
+        // line layers screen the cross-product comparison by single-precision
+        // bounds of R |d| (margins far above their rounding): |cross| <= c_lo is
+        // within R, |cross| > c_hi beyond it, only the rest is compared in 128
+        // bits.  The outline of polygon layers measured faster without it.
+        int64_t c_lo = -1, c_hi = INT64_MAX;   // no screen: every comparison exact
+        if (kScreen) {
+            const float rs = (float)(s.ext - s.off) * sqrtf((float)Ls);
+            c_lo = (int64_t)(rs * (1.0f - 0x1p-20f)) - 1;
+            c_hi = (int64_t)(rs * (1.0f + 0x1p-20f)) + 1;
+        }
         uint32_t c[4] = {0u, 0u, 0u, 0u};
         while (pm) {
             int l = __ffs(pm) - 1;
@@ -440,7 +444,7 @@ struct SegLeaf {
             for (int k = 0; k < 4; k++) {
                 if (k < s.nk && ((s.Uk[k] >> l) & 1u)) {
                     const int32_t sx = px + ((k & 1) ? s.off : -s.off), sy = py + ((k & 2) ? s.off : -s.off);
-                    const bool hit = near ? segment_within_rel(ax, ay, bx, by, dx, dy, Ls, sx, sy, s.R2)
+                    const bool hit = near ? segment_within_rel(ax, ay, bx, by, dx, dy, Ls, c_lo, c_hi, sx, sy, s.R2)
                                           : segment_within(o.x, o.y, o.z, o.w, s.bx0 + sx, s.by0 + sy, s.R2);
                     if (hit) c[k] |= 1u << l;
                 }
@@ -877,7 +881,6 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                         cm = rect_lanes(s, fbx.x, fbx.y, fbx.z, fbx.w);
                     }
                 }
-                certain_cover(s, fbx.x, fbx.y, fbx.z, fbx.w, lane);
                 uint32_t mm = __ballot_sync(kFull, reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
                 while (mm) {
                     int k = __ffs(mm) - 1;
@@ -981,7 +984,7 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
             stage<PointLeaf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
                              p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
         else
-            stage<SegLeaf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
+            stage<SegLeaf<kKind == HV_LAYER_LINES>>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
                            p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
         // Algorithm 2 over polygon boxes and edges
         if constexpr (kKind == HV_LAYER_POLYGONS) {
