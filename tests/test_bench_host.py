@@ -1,0 +1,30 @@
+"""Host-side logic of the benchmark: the measured-traffic record is used only
+while the kernel sources hash to the value stored beside it."""
+import os
+
+import bench
+
+
+def test_traffic_record_follows_kernel_hash(tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()
+    assert len(h) == 64
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    md = prof / bench.PROFILES[2]
+    md.write_text("summary\n\ntraffic_per_launch_bytes: 123456 kernel_sources_sha256 %s\n" % h)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    assert bench.measured_traffic(2) == 123456
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 64)
+    assert bench.measured_traffic(2) is None
+    assert bench.measured_traffic(5) is None
+
+
+def test_committed_profiles_parse():
+    # every render-kernel summary carries a traffic line in the expected form
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for name in bench.PROFILES.values():
+        lines = [ln for ln in open(os.path.join(root, "profiles", name)) if ln.startswith("traffic_per_launch_bytes:")]
+        assert len(lines) == 1
+        parts = lines[0].split()
+        assert int(parts[1]) > 0 and parts[2] == "kernel_sources_sha256" and len(parts[3]) == 64
