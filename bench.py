@@ -149,13 +149,23 @@ KERNEL_SOURCES = ("hv_render.cu", "hv_device.cuh", "hv_learned.cuh", "hv_interna
 PROFILES = {2: "k_render_points_gmm100M.md", 3: "k_render_lines_walk50M.md", 4: "k_render_polygons_star2M.md"}
 
 
+def _code_only(text):
+    """Source text without // and /* */ comments and without whitespace (the
+    files hashed below hold no string literal with comment markers)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return re.sub(r"\s+", "", text)
+
+
 def kernel_source_hash():
-    """sha256 over the sources the render kernel is compiled from."""
+    """sha256 over the code (comments and whitespace removed) of the sources
+    the render kernel is compiled from."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2005_12489_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2005_12489_gb300", "csrc", f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()
 
 

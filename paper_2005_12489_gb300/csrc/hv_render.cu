@@ -1,5 +1,6 @@
 // Tile rendering: tile cull, warp-cooperative traversal with early exit,
-// exact predicates and the output encode, fused in one kernel.
+// exact predicates and the output encode, fused in one kernel (one
+// instantiation per layer kind).
 //
 //   HiVision Algorithm 1 (SIBV): a pixel's value is the number of its four
 //   super-samples within distance R of some object (points, segments,
@@ -8,18 +9,21 @@
 //   polygon whose box contains it, that polygon's edges cross the ray from
 //   the centre an odd number of times.
 //
-// Work decomposition.  One CTA (8 warps) renders a 256 x 16 pixel strip of
-// one tile.  The CTA first culls the R-tree against the strip's box expanded
-// by R, breadth first, into a frontier of at most kFCap nodes in shared
-// memory (the deepest level that fits).  Each warp then takes 8 x 4 pixel
-// blocks (one pixel per lane, up to four samples per lane): it tests the
-// frontier against the box of its still-undecided samples, descends the
-// intersecting subtrees depth first (ballot of the 32 child boxes decides
-// which children to visit), evaluates the exact predicate on the objects of
-// each visited leaf, shrinks the box as samples are decided, and stops as
-// soon as every sample of the block is covered.  Results go to a per-pixel
-// byte array in shared memory; the epilogue encodes the strip (MASK bits,
-// COVERAGE bytes or RGBA) with coalesced 16-byte stores.
+// Work decomposition.  One CTA (8 warps) renders a strip of 256 x rows pixels
+// of one tile (rows = 16 for large batches, 8 or 4 for small ones).  The CTA
+// first culls the R-tree (or, with the learned index, the subtrees of the
+// key ranges the model finds) against the strip's box expanded by R, breadth
+// first, into a frontier of at most kFCap nodes in shared memory (the deepest
+// level that fits), binned by 8-pixel block column.  Each warp then takes
+// 8 x 4 pixel blocks (one pixel per lane, up to four samples per lane): it
+// tests its column's frontier entries against its still-undecided samples,
+// descends the intersecting subtrees depth first (a ballot over the 32 child
+// boxes decides which children to visit; for points, children that certainly
+// cover samples decide them on the spot), evaluates the exact predicate on
+// the records of each visited leaf, and stops as soon as every sample of the
+// block is decided.  Results go to a per-pixel byte array in shared memory;
+// the epilogue encodes the strip (MASK bits, COVERAGE bytes or RGBA) with
+// coalesced 16-byte stores.
 #include "hv_device.cuh"
 #include "hv_internal.h"
 #include "hv_learned.cuh"

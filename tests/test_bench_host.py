@@ -28,3 +28,10 @@ def test_committed_profiles_parse():
         assert len(lines) == 1
         parts = lines[0].split()
         assert int(parts[1]) > 0 and parts[2] == "kernel_sources_sha256" and len(parts[3]) == 64
+
+
+def test_code_only_ignores_comments_and_spacing():
+    a = "int x = 1;  // one\n/* block\n comment */ int y = x << 2;\n"
+    b = "int x = 1;\nint y = x << 2;  // shifted\n"
+    assert bench._code_only(a) == bench._code_only(b) == "intx=1;inty=x<<2;"
+    assert bench._code_only("int y = x << 3;") != bench._code_only("int y = x << 2;")
