@@ -247,7 +247,9 @@ int hv_render_tiles_counted(hv_layer* layer, const hv_tile_req* reqs, uint32_t n
                             int index_kind, const hv_style* style, void* out, uint64_t out_bytes,
                             int64_t* log, uint64_t log_cap, int64_t* log_count, void* stream);
 
-/* Number of kernels hv_render_tiles launches per call (for launch accounting). */
+/* Number of kernels hv_render_tiles launches per call (for launch accounting):
+ * 1 for point and linestring layers, 2 for polygon layers (outline, then
+ * fill); a call with host buffers launches that many per chunk of tiles. */
 int hv_render_launches(hv_layer* layer, int index_kind, uint32_t* launches);
 
 /* ---- serving (Sec. 4: MTVS task pool, IMMF, HPVE as one GPU loop) ------ */
