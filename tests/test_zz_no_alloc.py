@@ -48,3 +48,38 @@ def test_static_entry_matches_allocating_entry():
             hv.hv_layer_free(L)
     finally:
         hv.hv_destroy(ctx)
+
+
+@pytest.mark.parametrize("kind", ["lines", "polygons"])
+def test_static_entry_other_layer_kinds(kind):
+    """Segments (one launch) and polygons (an outline and a fill launch, the
+    second reading the first's output) through the staging array."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    ctx = hv.hv_create(0)
+    try:
+        if kind == "lines":
+            xy, off = gen.walk_lines(3_000, 20_000, seed=94, n_cities=10)
+            anchors = gen.segment_midpoints(xy, off, 2000, seed=95)
+            L = hv.hv_layer_load_linestrings(ctx, xy, off)
+        else:
+            xy, ro, po = gen.star_polygons(3_000, seed=96, k=8, rho_median=6e-4)
+            anchors = gen.polygon_centres(xy, ro, po)
+            L = hv.hv_layer_load_polygons(ctx, xy, ro, po)
+        hv.hv_layer_build_index(L, hv.HV_INDEX_RTREE)
+        style = hv.make_style((200, 30, 60), (20, 140, 250))
+        stream = torch.cuda.current_stream()
+        try:
+            for seed, n, mode in ((97, 40, hv.HV_MODE_RGBA), (98, 9, hv.HV_MODE_MASK)):
+                reqs = hv.make_requests(gen.density_tiles(anchors, n, 3, 14, [8, 24], seed=seed))
+                tb = hv.hv_tile_bytes(mode)
+                ref = torch.zeros((n, tb), dtype=torch.uint8, device="cuda")
+                hv.hv_render_tiles(L, reqs, n, mode, hv.HV_INDEX_RTREE, style, ref, ref.numel(), stream)
+                got = torch.full((n, tb), 0xAB, dtype=torch.uint8, device="cuda")
+                hv.hv_render_tiles_static(L, reqs, n, mode, hv.HV_INDEX_RTREE, style, got, got.numel(), stream)
+                stream.synchronize()
+                assert torch.equal(got, ref)
+        finally:
+            hv.hv_layer_free(L)
+    finally:
+        hv.hv_destroy(ctx)
