@@ -169,20 +169,47 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def measured_traffic(cfg):
-    """DRAM bytes (read + write) of one full-size launch of the render kernel,
-    from the committed ncu summary, if the kernel sources still hash to the
-    value recorded beside it; else None."""
+def _profile_record(cfg, key):
+    """The integer recorded under `key` in the committed ncu summary of the
+    workload's render kernel, if the kernel code still hashes to the value
+    recorded beside it; else None."""
     path = os.path.join(ROOT, "profiles", PROFILES.get(cfg, ""))
     if not os.path.isfile(path):
         return None
     want = kernel_source_hash()
     for ln in open(path):
-        if ln.startswith("traffic_per_launch_bytes:"):
+        if ln.startswith(key + ":"):
             parts = ln.split()
             if len(parts) >= 4 and parts[2] == "kernel_sources_sha256" and parts[3] == want:
                 return int(parts[1])
     return None
+
+
+def measured_instructions(cfg):
+    """Warp instructions one full-size launch (both launches of a polygon step)
+    executes, from the committed ncu summary (None once the kernel changed)."""
+    return _profile_record(cfg, "instructions_per_launch")
+
+
+def issue_peak():
+    """Issue-rate ceiling in G warp instructions/s: SMs x 4 schedulers x one
+    warp instruction per cycle at the maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    return sms * 4 * mhz * 1e6 / 1e9
+
+
+def measured_traffic(cfg):
+    """DRAM bytes (read + write) of one full-size launch of the render kernel,
+    from the committed ncu summary, if the kernel sources still hash to the
+    value recorded beside it; else None."""
+    return _profile_record(cfg, "traffic_per_launch_bytes")
 
 
 class Layer:
@@ -472,6 +499,19 @@ def run_gb300(args):
                     "frac": achieved / peak, "traffic": measured_traffic(args.config), "peak_kind": peak_kind,
                     "kernel": "k_render", "alg_bytes_per_tile": alg["per_tile"],
                     "alg_detail": alg}
+        # the committed counts are for one full-size launch of the default workload
+        full_size = args.points is None and args.r16 is None and n == WORKLOADS[args.config]["tiles_per_step"]
+        if roof is not None and not full_size:
+            roof["traffic"] = None
+        roof_issue = None
+        n_inst = measured_instructions(args.config) if full_size else None
+        if n_inst is not None:
+            ipk = issue_peak()
+            achieved_i = n_inst / (ms / 1000.0) / 1e9
+            roof_issue = {"bound": "alu", "achieved": achieved_i, "peak": ipk, "unit": "G warp-instructions/s",
+                          "frac": achieved_i / ipk, "instructions_per_launch": n_inst,
+                          "peak_basis": "SMs x 4 schedulers x 1 warp instruction/cycle x max SM clock",
+                          "note": "the integer pipe bounds this kernel; instruction count from the committed ncu summary"}
         e2e = None
         if not args.no_e2e:
             h_req = hv.make_requests(reqs)
@@ -498,7 +538,7 @@ def run_gb300(args):
                                l2="flushed between steps (512 MiB write); layer and 2.6 GB output exceed L2",
                                parallelism="replicas" if world > 1 else "single GPU"),
                 "pixel_queries_per_s": value * 65536,
-                "roofline": roof, "cpu_baseline": cpu, "cpu_rtree_mt": cpu_mt, "e2e": e2e,
+                "roofline": roof, "roofline_issue": roof_issue, "cpu_baseline": cpu, "cpu_rtree_mt": cpu_mt, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                 "index_timed": args.index, "learned": learned, "latency": lat,
                 "wall_s_timed_region": wall, "step_ms": step_ms,

@@ -24,10 +24,11 @@ def test_committed_profiles_parse():
     # every render-kernel summary carries a traffic line in the expected form
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     for name in bench.PROFILES.values():
-        lines = [ln for ln in open(os.path.join(root, "profiles", name)) if ln.startswith("traffic_per_launch_bytes:")]
-        assert len(lines) == 1
-        parts = lines[0].split()
-        assert int(parts[1]) > 0 and parts[2] == "kernel_sources_sha256" and len(parts[3]) == 64
+        for key in ("traffic_per_launch_bytes:", "instructions_per_launch:"):
+            lines = [ln for ln in open(os.path.join(root, "profiles", name)) if ln.startswith(key)]
+            assert len(lines) == 1, (name, key)
+            parts = lines[0].split()
+            assert int(parts[1]) > 0 and parts[2] == "kernel_sources_sha256" and len(parts[3]) == 64
 
 
 def test_code_only_ignores_comments_and_spacing():
