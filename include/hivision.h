@@ -104,10 +104,17 @@ typedef struct hv_style {
     uint8_t fill_rgba[4];  /* polygon interiors */
 } hv_style;
 
+/* hv_build_opts.learned_hidden value: train no MLP residual. */
+#define HV_LEARNED_NO_MLP 0xFFFFFFFFu
+
 typedef struct hv_build_opts {
-    uint32_t learned_segments;   /* piecewise-linear pieces (0 = default 65536) */
-    uint32_t learned_hidden;     /* MLP hidden width, <= 32 (0 = default 16) */
-    uint32_t learned_steps;      /* training steps (0 = default 400) */
+    uint32_t learned_segments;   /* piecewise-linear pieces (0 = one piece per
+                                    512 sorted keys) */
+    uint32_t learned_hidden;     /* 0: pieces with the residual MLP 5 -> 16 ->
+                                    16 -> 1 (kept where it narrows a piece's
+                                    bound); HV_LEARNED_NO_MLP: linear pieces
+                                    only; other values are reserved */
+    uint32_t learned_steps;      /* training steps (0 = default 300) */
     uint32_t learned_seed;       /* initialisation seed */
     uint32_t max_error;          /* accept the learned index only if its
                                     position error bound is <= this (0 = 4096) */

@@ -330,6 +330,7 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
     // any other value enables it as well
     const int H = kDefaultHidden;
     int steps = opts && opts->learned_steps ? (int)opts->learned_steps : kDefaultSteps;
+    if (opts && opts->learned_hidden == HV_LEARNED_NO_MLP) steps = 0;   // linear pieces only
     uint32_t seed = opts ? opts->learned_seed : 0;
     uint64_t *kb;
     float *pa, *pc, *pinv;

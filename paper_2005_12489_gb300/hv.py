@@ -23,6 +23,7 @@ STATUS_NAMES = ["HV_OK", "HV_EINVAL", "HV_ERANGE", "HV_ENOMEM", "HV_ECUDA", "HV_
 HV_MODE_MASK, HV_MODE_COVERAGE, HV_MODE_RGBA = 0, 1, 2
 HV_LAYER_POINTS, HV_LAYER_LINES, HV_LAYER_POLYGONS = 0, 1, 2
 HV_INDEX_RTREE, HV_INDEX_LEARNED = 1, 2
+HV_LEARNED_NO_MLP = 0xFFFFFFFF     # hv_build_opts.learned_hidden: linear pieces only
 
 REQ_DTYPE = np.dtype([("x", "<u4"), ("y", "<u4"), ("r16", "<u2"), ("z", "u1"), ("mode", "u1"),
                       ("layer", "<u4")])

@@ -112,9 +112,15 @@ def test_learned_points_tiles(ctx, mlp):
     reqs = gen.density_tiles(pts, 150, 0, 19, [1, 8, 32, 100, 600], seed=34)
     L = hv.hv_layer_load_points(ctx, pts)
     opts = hv.hv_build_opts()
-    opts.learned_steps = 200 if mlp else 0
+    if mlp:
+        opts.learned_steps = 200
+    else:
+        opts.learned_hidden = hv.HV_LEARNED_NO_MLP
     hv.hv_layer_build_index(L, hv.HV_INDEX_RTREE | hv.HV_INDEX_LEARNED, opts)
     try:
+        info = hv.info_dict(L)
+        if not mlp:
+            assert info["learned_mlp"] == 0 and info["learned_error"] == info["learned_error_linear"]
         for mode in MODES:
             a = render_dev(L, reqs, mode, hv.HV_INDEX_LEARNED)
             b = render_dev(L, reqs, mode, hv.HV_INDEX_RTREE)
