@@ -324,11 +324,12 @@ def run_reference(args):
         if step >= args.warmup:
             times.append(dt)
     value = n_sample * len(times) / sum(times)
-    line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": 0, "steps": args.steps,
+    # n_gpus: the launch's N (this arm itself runs on one host core)
+    line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "impl": "reference",
-            "config": dict(WORKLOADS[args.config], sample_tiles_per_step=n_sample),
+            "config": dict(WORKLOADS[args.config], n_objects=lay.n_objects, sample_tiles_per_step=n_sample),
             "cpu_baseline": {"value": value, "unit": "tiles/s", "cores": 1, "kind": "oracle",
                              "sample": "%d tiles per step of the %d-tile batch, all %d %s"
                                        % (n_sample, len(reqs), lay.n_objects, NOUN[lay.kind])},

@@ -36,3 +36,24 @@ def test_code_only_ignores_comments_and_spacing():
     b = "int x = 1;\nint y = x << 2;  // shifted\n"
     assert bench._code_only(a) == bench._code_only(b) == "intx=1;inty=x<<2;"
     assert bench._code_only("int y = x << 3;") != bench._code_only("int y = x << 2;")
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference runs the oracle on the host and prints one
+    JSON line with the contract's keys (no GPU needed)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "1", "--points", "200000"], capture_output=True, text=True, timeout=600,
+                         cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "tiles/s" and line["value"] > 0
+    assert line["higher_is_better"] is True and line["steps"] == 1 and line["warmup"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "tiles/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["n_objects"] == 200000 and "workload" in line["config"]
