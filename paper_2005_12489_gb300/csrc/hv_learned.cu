@@ -1,9 +1,10 @@
-// Learned position index (spec layer on top of HiVision's R-tree
-// lookups, Sec. 3.1): a piecewise-linear + MLP model of an object's position
-// in the Hilbert-sorted order as a function of its key, trained on the device
-// with the kernels below, with a per-piece error bound measured over every
-// key.  Objects with extent are found through their centre key within a halo;
-// the few whose half-extent exceeds the halo go to a small side R-tree.
+// Learned position index (a layer on top of HiVision's R-tree lookups,
+// Sec. 3.1, with no counterpart in the paper): a piecewise-linear + MLP model
+// of an object's position in the Hilbert-sorted order as a function of its
+// key, trained on the device with the kernels below, with a per-piece error
+// bound measured over every key.  Objects with extent are found through their
+// centre key within a halo; the few whose half-extent exceeds the halo go to
+// a small side R-tree.
 #include <math.h>
 
 #include "hv_device.cuh"
