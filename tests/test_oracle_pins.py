@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from oracle import brute
-from geom import (at, centre, coverage_fill, coverage_value, golden, lines_to_arrays,
+from geom import (at, centre, coverage_fill, coverage_value, golden, lines_to_arrays, ps,
                   polys_to_arrays, random_cluster_points, random_star_polygons,
                   random_walk_lines, ring_px)
 
@@ -355,3 +355,35 @@ def test_rejects_out_of_range():
             oracle.render_points(pts, [bad], MASK)
     with pytest.raises(ValueError):
         oracle.render_points(np.array([[1 << 30, 0]], dtype=np.int64).astype(np.int32), [[0, 0, 0, 16]], MASK)
+
+
+def test_rgba_values_by_hand():
+    """RGBA values worked out by hand.  Points placed exactly on 1..4 of a
+    pixel's super-samples, with a radius (1/16 px) too small to reach any
+    other sample, give v = 1..4 and alpha (255 v + 2) >> 2 = 64, 128, 191,
+    255 in the line colour.  A square whose west edge passes through a
+    pixel's two west super-samples covers exactly those two (v = 2) and fills
+    the pixel (its centre lies inside), so the pixel is the composite
+    ((line * 128 + fill * 127 + 127) // 255 per channel, 255); the pixel to
+    its east is filled with v = 0, i.e. the fill colour itself."""
+    z, tx, ty = 10, 300, 400
+    q = ps(z) // 4
+    line, fill = STYLE[:3], STYLE[4:7]
+    for v, i in zip((1, 2, 3, 4), (40, 60, 80, 100)):
+        cx, cy = centre(z, tx, ty, i, 50)
+        samples = [(cx - q, cy - q), (cx + q, cy - q), (cx - q, cy + q), (cx + q, cy + q)][:v]
+        pts = np.array(samples, dtype=np.int32)
+        got = oracle.render_points(pts, [[z, tx, ty, 1]], RGBA, STYLE)[0].reshape(256, 256, 4)
+        assert tuple(int(x) for x in got[50, i]) == line + ((255 * v + 2) >> 2,)
+        assert int(np.count_nonzero(got[:, :, 3])) == 1          # no other pixel is reached
+    i, j = 120, 130
+    cx, cy = centre(z, tx, ty, i, j)
+    x_edge = cx - q
+    square = [(x_edge, cy - 5 * ps(z)), (x_edge + 40 * ps(z), cy - 5 * ps(z)),
+              (x_edge + 40 * ps(z), cy + 5 * ps(z)), (x_edge, cy + 5 * ps(z))]
+    xy, ro, po = polys_to_arrays([[square]])
+    got = oracle.render_polygons(xy, ro, po, [[z, tx, ty, 1]], RGBA, STYLE)[0].reshape(256, 256, 4)
+    comp = tuple((l * 128 + f * 127 + 127) // 255 for l, f in zip(line, fill)) + (255,)
+    assert tuple(int(x) for x in got[j, i]) == comp
+    assert tuple(int(x) for x in got[j, i + 1]) == fill + (255,)
+    assert tuple(int(x) for x in got[j, i - 1]) == (0, 0, 0, 0)
