@@ -60,3 +60,21 @@ def test_create_without_gpu_reports_error(lib):
     with pytest.raises(lib.HVError) as e:
         lib.hv_create(0)
     assert e.value.status in (lib.HV_ECUDA, lib.HV_EINVAL)
+
+
+def test_missing_library_fails_loudly():
+    """Without the CUDA library every call raises: there is no CPU fallback."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2005_12489_gb300 import hv\n"
+            "hv.LIB_PATH = '/nonexistent/libhivision.so'\n"
+            "try:\n"
+            "    hv.hv_create(0)\n"
+            "except ImportError as e:\n"
+            "    print('raised', e)\n"
+            "    sys.exit(0)\n"
+            "sys.exit(3)\n" % root)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and "not built" in out.stdout, out.stdout + out.stderr
