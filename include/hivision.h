@@ -317,21 +317,27 @@ int hv_server_stats(hv_server* srv, uint64_t* batches, uint64_t* tiles, uint64_t
 
 /* ---- rendering without allocation (no counterpart in the paper) --------- */
 
-/* hv_render_tiles for callers that cannot allocate device memory: code that
- * runs while a stream is captured into a CUDA graph (cudaMalloc is not
- * allowed there), hosts whose device memory belongs to another allocator,
- * and latency-critical paths that cannot take the device-wide synchronisation
- * of cudaMalloc / cudaFree.  It calls no allocator: requests (host or device
- * memory, at most 4096 per call) are staged in a fixed 64 KiB device array
- * inside the library, which every device that loads the library holds until
- * the process exits; `out` must be device memory of n * hv_tile_bytes(mode)
- * bytes, 16-byte aligned, and the call is asynchronous on `stream`.  The first
- * call on a device looks up that array's address (cudaGetSymbolAddress) with
- * the device current; make that first call before any stream capture.  All
- * calls share the one array, which keeps the last call's requests: calls whose
- * work overlaps on the GPU (other streams, other threads) race on it, so
- * order them on one stream or synchronise between them.  More than 4096 tiles
- * -> HV_EINVAL; other errors as hv_render_tiles. */
+/* hv_render_tiles for callers that cannot allocate device memory: hosts whose
+ * device memory is owned by another allocator or memory pool (a cudaMalloc of
+ * their own would fail, or fragment the pool), and latency-critical paths that
+ * cannot take the device-wide synchronisation that cudaMalloc / cudaFree may
+ * imply.  It calls no allocator and takes at most 4096 tiles per call.
+ * Requests in device memory are read where they are.  Requests in host
+ * memory are staged in a fixed 64 KiB device array inside the library (4096
+ * requests), which every device that loads the library holds until the
+ * process exits.  `out` must be device
+ * memory of n * hv_tile_bytes(mode) bytes, 16-byte aligned; the call is
+ * asynchronous on `stream`.
+ * Set-up: the first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current) and keeps it; make that
+ * first call before any stream capture.  The address belongs to the device's
+ * primary context: after a device reset the library's handles and this
+ * address are all invalid.
+ * Sharing: all calls with host requests use the one array, which keeps the
+ * last call's requests; such calls whose work overlaps on the GPU (other
+ * streams, other threads) race on it, so order them on one stream or
+ * synchronise between them.
+ * More than 4096 tiles -> HV_EINVAL; other errors as hv_render_tiles. */
 int hv_render_tiles_static(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode,
                            int index_kind, const hv_style* style, void* out, uint64_t out_bytes,
                            void* stream);

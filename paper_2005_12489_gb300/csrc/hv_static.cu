@@ -3,12 +3,12 @@
 //
 // hv_render_tiles stages host requests (and host outputs) through device
 // buffers that the library allocates on demand with cudaMalloc.  Some callers
-// cannot allow that: code running while a stream is being captured into a
-// CUDA graph (cudaMalloc is not permitted there), hosts whose device memory
-// is owned by another allocator or pool, and latency-critical paths where the
-// implicit device synchronisation of cudaMalloc / cudaFree is unacceptable.
-// This entry point uses no allocation at all: the request staging area is a
-// fixed file-scope device array, and the caller provides the output buffer.
+// cannot allow that: hosts whose device memory is owned by another allocator
+// or pool, and latency-critical paths where the device synchronisation that
+// cudaMalloc / cudaFree may imply is unacceptable.  This entry point uses no
+// allocation at all: device requests are read in place, host requests are
+// staged in a fixed file-scope device array, and the caller provides the
+// output buffer.
 #include <mutex>
 
 #include "hv_internal.h"
@@ -93,11 +93,12 @@ int hv_render_tiles_static(hv_layer* layer, const hv_tile_req* reqs, uint32_t n,
             }
         }
     }
+    cudaStream_t st = (cudaStream_t)stream;
+    // device requests need no staging: the kernel reads (and checks) them
+    if (dev_reqs) return launch_render(L, reqs, n, mode, index_kind, style, (uint8_t*)out, st);
     hv_tile_req* area = nullptr;
     HV_TRY(static_area(L->ctx->device, &area));
-    cudaStream_t st = (cudaStream_t)stream;
-    HV_CUDA(cudaMemcpyAsync(area, reqs, (uint64_t)n * sizeof(hv_tile_req),
-                            dev_reqs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    HV_CUDA(cudaMemcpyAsync(area, reqs, (uint64_t)n * sizeof(hv_tile_req), cudaMemcpyHostToDevice, st));
     return launch_render(L, area, n, mode, index_kind, style, (uint8_t*)out, st);
 }
 

@@ -1,10 +1,12 @@
 """The allocation-free entry point against the allocating one.
 
 hv_render_tiles_static serves callers that may not allocate device memory
-(for example inside a stream capture, or when another allocator owns the
-device): it stages requests in a fixed device array of the library instead
-of cudaMalloc'd scratch.  Its tiles must equal hv_render_tiles' exactly, call
-after call, although every call reuses the same staging array.
+(when another allocator or pool owns the device's memory, or on paths that
+cannot take the synchronisation an allocation may imply): it stages host
+requests in a fixed device array of the library instead of cudaMalloc'd
+scratch, and reads device requests in place.  Its tiles must equal
+hv_render_tiles' exactly, call after call, although every call with host
+requests reuses the same staging array.
 """
 import numpy as np
 import pytest
@@ -39,6 +41,23 @@ def test_static_entry_matches_allocating_entry():
                 hv.hv_render_tiles_static(L, reqs, n, mode, hv.HV_INDEX_RTREE, style, got, got.numel(), stream)
                 stream.synchronize()
                 assert torch.equal(got, ref)
+            # the whole staging array (4096 requests), then device-resident
+            # requests (read in place) twice in a row
+            full = hv.make_requests(gen.density_tiles(pts, 4096, 2, 16, [4, 16, 40], seed=99))
+            ref = torch.zeros((4096, 8192), dtype=torch.uint8, device="cuda")
+            hv.hv_render_tiles(L, full, 4096, hv.HV_MODE_MASK, hv.HV_INDEX_RTREE, None, ref, ref.numel(), stream)
+            got = torch.full((4096, 8192), 0xAB, dtype=torch.uint8, device="cuda")
+            hv.hv_render_tiles_static(L, full, 4096, hv.HV_MODE_MASK, hv.HV_INDEX_RTREE, None, got,
+                                      got.numel(), stream)
+            stream.synchronize()
+            assert torch.equal(got, ref)
+            d_full = torch.from_numpy(full.view(np.uint8).copy()).cuda()
+            for n in (4096, 123):
+                got.fill_(0xCD)
+                hv.hv_render_tiles_static(L, d_full, n, hv.HV_MODE_MASK, hv.HV_INDEX_RTREE, None, got,
+                                          got.numel(), stream)
+                stream.synchronize()
+                assert torch.equal(got[:n], ref[:n])
             with pytest.raises(hv.HVError) as e:
                 big = hv.make_requests(np.tile([[3, 1, 1, 16]], (4097, 1)))
                 hv.hv_render_tiles_static(L, big, 4097, hv.HV_MODE_MASK, hv.HV_INDEX_RTREE, None, got,
