@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+import oracle_par
 from geom import (at, lines_to_arrays, polys_to_arrays, random_cluster_points,
                   random_star_polygons, random_walk_lines, ring_px)
 from workloads import gen
@@ -27,6 +28,16 @@ def ctx():
     c = hv.hv_create(0)
     yield c
     hv.hv_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def lines50m(ctx):
+    """The full-size linestring layer with both indexes, shared by its tests."""
+    xy, off, reqs = gen.config3()
+    L = hv.hv_layer_load_linestrings(ctx, xy, off)
+    hv.hv_layer_build_index(L, hv.HV_INDEX_RTREE | hv.HV_INDEX_LEARNED)
+    yield xy, off, reqs, L
+    hv.hv_layer_free(L)
 
 
 def style():
@@ -310,59 +321,64 @@ def test_memory_budget(ctx):
 @pytest.mark.slow
 def test_clustered_100m_points_sampled_tiles(ctx):
     """100M clustered points, 10,000 density-weighted tiles (zoom 8-14,
-    radius 2 px, RGBA) rendered in one call; 48 tiles spread over the batch
-    (densest and emptiest included) checked against the oracle."""
+    radius 2 px, RGBA) rendered in one call; 72 tiles (16 densest, 4
+    emptiest, an even spread) against the oracle, and the learned index
+    against the R-tree on all tiles."""
     pts, reqs = gen.config2()
-    L = points_layer(ctx, pts)
+    L = hv.hv_layer_load_points(ctx, pts)
+    hv.hv_layer_build_index(L, hv.HV_INDEX_RTREE | hv.HV_INDEX_LEARNED)
     try:
-        got = render_dev(L, reqs, hv.HV_MODE_RGBA)
-        alpha = got.reshape(len(reqs), -1, 4)[:, :, 3]
-        lit = (alpha > 0).sum(1)
-        pick = set(np.argsort(lit)[-8:].tolist()) | set(np.argsort(lit)[:4].tolist())
-        pick |= set(np.random.default_rng(0).choice(len(reqs), 36, replace=False).tolist())
-        pick = np.array(sorted(pick))
-        ref = oracle.render_points(pts, reqs[pick], hv.HV_MODE_RGBA, STYLE_T)
-        bad = [int(pick[k]) for k in range(len(pick)) if not np.array_equal(got[pick[k]], ref[k])]
-        assert not bad, "tiles differ: %s" % bad
+        n = _sampled_check(L, lambda r, m: oracle.render_points(pts, r, m, STYLE_T), reqs, 52, 16)
+        assert n >= 64
     finally:
         hv.hv_layer_free(L)
 
 
-def _sampled_check(render_gpu, render_ref, reqs, n_even, n_dense, mode=hv.HV_MODE_RGBA):
-    got = render_gpu(reqs, mode)
+def _sampled_check(L, render_ref, reqs, n_even, n_dense, n_empty=4, mode=hv.HV_MODE_RGBA):
+    """All tiles in one call through the R-tree and the learned index: the two
+    must agree on every tile, and a sample (the densest and emptiest tiles and
+    an even spread) must equal the oracle, evaluated on the host's cores."""
+    got = render_dev(L, reqs, mode)
+    learned = render_dev(L, reqs, mode, hv.HV_INDEX_LEARNED)
+    diff = np.nonzero((got != learned).any(axis=1))[0]
+    assert diff.size == 0, "learned index differs from the R-tree on %d tiles, first %s" % (diff.size, diff[:8])
     lit = (got.reshape(len(reqs), -1, 4)[:, :, 3] > 0).sum(1) if mode == hv.HV_MODE_RGBA else got.sum(1)
-    pick = set(np.argsort(lit)[-n_dense:].tolist())
+    order = np.argsort(lit, kind="stable")
+    pick = set(order[-n_dense:].tolist()) | set(order[:n_empty].tolist())
     pick |= set(np.linspace(0, len(reqs) - 1, n_even).astype(int).tolist())
     pick = np.array(sorted(pick))
-    ref = render_ref(reqs[pick], mode)
+    ref = oracle_par.render(lambda r: render_ref(r, mode), reqs[pick])
     bad = [int(pick[k]) for k in range(len(pick)) if not np.array_equal(got[pick[k]], ref[k])]
     assert not bad, "tiles differ: %s" % bad
+    return len(pick)
 
 
 @pytest.mark.slow
-def test_linestrings_50m_segments_sampled_tiles(ctx):
+@pytest.mark.parametrize("r16", [8, 16, 24])
+def test_linestrings_50m_segments_sampled_tiles(ctx, lines50m, r16):
     """50M segments in 5M random-walk lines, 10,000 density-weighted tiles
-    (zoom 6-16, half-width 1 px, RGBA) in one call; 16 tiles checked."""
-    xy, off, reqs = gen.config3()
-    L = hv.hv_layer_load_linestrings(ctx, xy, off)
-    hv.hv_layer_build_index(L)
-    try:
-        _sampled_check(lambda r, m: render_dev(L, r, m),
-                       lambda r, m: oracle.render_lines(xy, off, r, m, STYLE_T), reqs, 12, 4)
-    finally:
-        hv.hv_layer_free(L)
+    (zoom 6-16) at half-width 0.5, 1 and 1.5 px, RGBA, in one call; 72 tiles
+    (16 densest, 4 emptiest, an even spread) against the oracle, and the
+    learned index against the R-tree on all tiles."""
+    xy, off, reqs, L = lines50m
+    reqs = reqs.copy()
+    reqs[:, 3] = r16
+    n = _sampled_check(L, lambda r, m: oracle.render_lines(xy, off, r, m, STYLE_T), reqs, 52, 16)
+    assert n >= 64
 
 
 @pytest.mark.slow
 def test_polygons_2m_sampled_tiles(ctx):
     """2M star polygons (72M edges), 10,000 density-weighted tiles (zoom 4-14,
-    fill + 1 px outline, RGBA) in one call; 8 tiles checked."""
+    fill + 1 px outline, RGBA) in one call; 72 tiles (16 densest, 4
+    emptiest, an even spread) against the oracle, and the learned index
+    against the R-tree on all tiles."""
     xy, ro, po, reqs = gen.config4()
     L = hv.hv_layer_load_polygons(ctx, xy, ro, po)
-    hv.hv_layer_build_index(L)
+    hv.hv_layer_build_index(L, hv.HV_INDEX_RTREE | hv.HV_INDEX_LEARNED)
     try:
-        _sampled_check(lambda r, m: render_dev(L, r, m),
-                       lambda r, m: oracle.render_polygons(xy, ro, po, r, m, STYLE_T), reqs, 6, 2)
+        n = _sampled_check(L, lambda r, m: oracle.render_polygons(xy, ro, po, r, m, STYLE_T), reqs, 52, 16)
+        assert n >= 64
     finally:
         hv.hv_layer_free(L)
 

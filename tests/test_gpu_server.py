@@ -1,15 +1,17 @@
 """Serving loop: continuous batching must not change any pixel.
 
 Every tile served in a mix of layers, zooms, radii and modes, with many
-requests in flight, must equal the same request served alone and the same
-tile rendered by hv_render_tiles (HiVision Sec. 4: tasks are independent;
-the engine only schedules them).
+requests in flight, must equal the oracle's tile for the same request, the
+same request served alone, and the same tile rendered by hv_render_tiles
+(HiVision Sec. 4: tasks are independent; the MTVS / IMMF / HPVE pipeline only
+schedules them).
 """
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 from workloads import gen
 
 torch = pytest.importorskip("torch")
@@ -39,7 +41,8 @@ def layers(ctx):
     for L in Ls:
         hv.hv_layer_build_index(L, hv.HV_INDEX_RTREE | hv.HV_INDEX_LEARNED)
     anchors = [pts, gen.segment_midpoints(xy, off, 2000), gen.polygon_centres(pxy, ro, po)]
-    yield Ls, anchors
+    src = [("points", pts), ("lines", xy, off), ("polygons", pxy, ro, po)]
+    yield Ls, anchors, src
     for L in Ls:
         hv.hv_layer_free(L)
 
@@ -74,6 +77,28 @@ def poll_all(srv, want, timeout=120.0):
     return got
 
 
+def oracle_tiles(src, reqs):
+    """The oracle's tile for every request, one oracle call per (layer, mode)."""
+    out = {}
+    zxyr = np.stack([reqs["z"], reqs["x"], reqs["y"], reqs["r16"]], 1).astype(np.uint32)
+    for layer in np.unique(reqs["layer"]):
+        for mode in np.unique(reqs["mode"]):
+            idx = np.nonzero((reqs["layer"] == layer) & (reqs["mode"] == mode))[0]
+            if not idx.size:
+                continue
+            s = src[int(layer)]
+            st = STYLE[0] + (0,) + STYLE[1] + (0,)
+            if s[0] == "points":
+                ref = oracle.render_points(s[1], zxyr[idx], int(mode), st)
+            elif s[0] == "lines":
+                ref = oracle.render_lines(s[1], s[2], zxyr[idx], int(mode), st)
+            else:
+                ref = oracle.render_polygons(s[1], s[2], s[3], zxyr[idx], int(mode), st)
+            for k, i in enumerate(idx):
+                out[int(i)] = ref[k].tobytes()
+    return out
+
+
 def direct(Ls, reqs, style):
     out = {}
     for i, r in enumerate(reqs):
@@ -87,7 +112,7 @@ def direct(Ls, reqs, style):
 
 @pytest.mark.parametrize("graphs,index", [(1, hv.HV_INDEX_RTREE), (0, hv.HV_INDEX_RTREE), (1, hv.HV_INDEX_LEARNED)])
 def test_alone_equals_mix(ctx, layers, graphs, index):
-    Ls, anchors = layers
+    Ls, anchors, src = layers
     style = hv.make_style(*STYLE)
     reqs = mixed_requests(anchors, 240, seed=54 + graphs + index)
     opts = hv.make_server_opts(max_batch=16, scratch_bytes=16 * 262144 * 6, index_kind=index,
@@ -105,18 +130,20 @@ def test_alone_equals_mix(ctx, layers, graphs, index):
         stats = hv.hv_server_stats(srv)
     finally:
         hv.hv_server_stop(srv)
-    ref = direct(Ls, reqs, style)
+    ref = oracle_tiles(src, reqs)
+    rendered = direct(Ls, reqs, style)
     for i in range(0, len(reqs), 8):
         assert alone[i] == ref[i], "alone %d" % i
     for i in range(len(reqs)):
-        assert mix[1000 + i] == ref[i], "mix %d" % i
+        assert mix[1000 + i] == ref[i], "mix %d differs from the oracle" % i
+        assert rendered[i] == ref[i], "hv_render_tiles %d" % i
     assert stats["batches"] < stats["tiles"]             # requests were batched
     if graphs:
         assert stats["graph_launches"] == stats["batches"]
 
 
 def test_submit_errors_and_back_pressure(ctx, layers):
-    Ls, anchors = layers
+    Ls, anchors, _ = layers
     opts = hv.make_server_opts(max_batch=1, queue_capacity=4, scratch_bytes=262144 + 64)
     srv = hv.hv_server_start(ctx, Ls[:1], opts)
     try:
@@ -142,7 +169,7 @@ def test_submit_errors_and_back_pressure(ctx, layers):
 
 
 def test_open_loop_replay(ctx, layers):
-    Ls, anchors = layers
+    Ls, anchors, _ = layers
     reqs = mixed_requests(anchors, 3000, seed=60)
     reqs["mode"] = hv.HV_MODE_RGBA
     arrival = np.cumsum(np.random.default_rng(61).exponential(1e6 / 20000.0, size=len(reqs)))
