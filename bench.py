@@ -57,7 +57,7 @@ def parse():
                          "5: serving an open-loop request stream over resident layers")
     ap.add_argument("--rates", default="5000,10000,20000,50000,inf",
                     help="config 5: request rates (tiles/s), 'inf' = all at once")
-    ap.add_argument("--requests", type=int, default=40_000, help="config 5: requests per rate")
+    ap.add_argument("--requests", type=int, default=100_000, help="config 5: requests per rate")
     ap.add_argument("--serve-points", type=int, default=1_000_000_000)
     ap.add_argument("--serve-segments", type=int, default=200_000_000)
     ap.add_argument("--r16", type=int, default=None)
@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--index", default="rtree", choices=["rtree", "learned"],
                     help="index timed for the headline value (both are reported)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the clustered-points line, without the blocks of the other workloads")
     ap.add_argument("--profile-steps", action="store_true",
                     help="only warm-up + steps, no baselines (for ncu launch lists)")
     ap.add_argument("--volume-sweep", default=None,
@@ -377,30 +379,101 @@ def algorithmic_bytes_per_tile(hv, layer, reqs_dev_np, torch, n_sample, lay):
             "leaf_visits_per_pixel": leaf_visits / 65536, "sample_tiles": k}
 
 
-def run_gb300(args):
+def _timed(step, flush, stream, k_steps, warm=2):
+    """Mean device time (ms) of k_steps calls of step(), each bracketed by CUDA
+    events on `stream`, the L2 flushed before each."""
+    import torch
+    for _ in range(warm):
+        flush.fill_(1)
+        step()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_steps)]
+    for k in range(k_steps):
+        flush.fill_(k & 255)
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def _latency(hv, torch, layer, d_req, n, mode, index, style, stream, n_tiles=300):
+    """Per-tile latency: batch-1 calls, each timed with CUDA events."""
+    tb = hv.hv_tile_bytes(mode)
+    idx = np.linspace(0, n - 1, n_tiles).astype(np.int64)
+    one = torch.empty((1, tb), dtype=torch.uint8, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_tiles)]
+    req_rows = d_req.view(n, 16)
+    for k, t in enumerate(idx):
+        evs[k][0].record(stream)
+        hv.hv_render_tiles(layer, req_rows[int(t)], 1, mode, index, style, one, one.numel(), stream)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    lat = np.array([a.elapsed_time(b) for a, b in evs])
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "tiles": n_tiles, "form": "batch-1 calls, device buffers"}
+
+
+def _learned_info(info):
+    return {"error_bound": info.learned_error, "error_bound_linear": info.learned_error_linear,
+            "error_bound_mlp": info.learned_error_mlp, "mean_error": info.learned_mean_error,
+            "pieces": info.learned_pieces, "pieces_with_mlp": info.learned_mlp,
+            "mean_window": info.learned_mean_window, "mean_window_linear": info.learned_mean_window_linear,
+            "halo": info.learned_halo, "side_tree_objects": info.learned_outliers, "train_ms": info.train_ms}
+
+
+def _roofline(alg, n, ms, cfg, full_size, launch_ms=None):
+    """HBM roofline of the render kernel(s): algorithmic bytes per launch over
+    the launch time (the step's device time: one call is one launch, two for
+    polygon layers)."""
+    if alg is None:
+        return None
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg["per_tile"] * n / (ms / 1000.0) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": measured_traffic(cfg) if full_size else None, "peak_kind": peak_kind,
+            "kernel": "k_render", "alg_bytes_per_tile": alg["per_tile"], "alg_detail": alg}
+
+
+def _roofline_issue(cfg, ms, full_size):
+    n_inst = measured_instructions(cfg) if full_size else None
+    if n_inst is None:
+        return None
+    ipk = issue_peak()
+    achieved_i = n_inst / (ms / 1000.0) / 1e9
+    return {"bound": "alu", "achieved": achieved_i, "peak": ipk, "unit": "G warp-instructions/s",
+            "frac": achieved_i / ipk, "instructions_per_launch": n_inst,
+            "peak_basis": "SMs x 4 schedulers x 1 warp instruction/cycle x max SM clock",
+            "note": "the integer pipe bounds this kernel; instruction count from the committed ncu summary"}
+
+
+def measure_batch(args, cfg, steps, warmup, dist=None, headline=False, r16_sweep=None):
+    """One batch workload (clustered points, linestrings or polygons): a step
+    renders the whole batch of tiles with one hv_render_tiles call (device
+    requests and output).  Returns the JSON dict of the workload; with
+    `headline` the timed region follows the full contract (barrier, clocks,
+    max over ranks) and extras run on rank 0 only."""
     import torch
     from paper_2005_12489_gb300 import hv
 
     rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    w = WORKLOADS[cfg]
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    lay = workload(args, rank)
+    a = argparse.Namespace(**vars(args))
+    if not headline:
+        a.points, a.r16, a.tiles = None, None, w["tiles_per_step"]
+    lay = Layer(cfg, a, rank)
     reqs = lay.reqs
     ctx = hv.hv_create(local)
     layer = lay.load(hv, ctx)
     want_learned = (not args.no_learned) or args.index == "learned"
     hv.hv_layer_build_index(layer, hv.HV_INDEX_RTREE | (hv.HV_INDEX_LEARNED if want_learned else 0))
     info = hv.hv_layer_info_get(layer)
-    main_index = hv.HV_INDEX_LEARNED if args.index == "learned" else hv.HV_INDEX_RTREE
+    main_index = hv.HV_INDEX_LEARNED if (headline and args.index == "learned") else hv.HV_INDEX_RTREE
     mode = hv.HV_MODE_RGBA
     tb = hv.hv_tile_bytes(mode)
     n = len(reqs)
@@ -411,19 +484,18 @@ def run_gb300(args):
     stream = torch.cuda.current_stream()
     launches_per_step = hv.hv_render_launches(layer, main_index)
 
-    def step(index=main_index):
-        hv.hv_render_tiles(layer, d_req, n, mode, index, style, d_out, d_out.numel(), stream)
+    def step(index=main_index, reqs_dev=d_req):
+        hv.hv_render_tiles(layer, reqs_dev, n, mode, index, style, d_out, d_out.numel(), stream)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.fill_(1)
         step()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     clocks = Clocks(local)
     barrier()
     clocks.start()
     t0 = time.perf_counter()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.fill_(k & 255)            # L2 flush between steps (not timed)
         ev[k][0].record(stream)
         step()
@@ -431,138 +503,149 @@ def run_gb300(args):
     barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    step_ms = [x.elapsed_time(y) for x, y in ev]
     ms = sum(step_ms) / len(step_ms)
-
-    def timed_steps(index, k_steps):
-        for _ in range(2):
-            step(index)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(k_steps)]
-        for k in range(k_steps):
-            flush.fill_(k & 255)
-            evs[k][0].record(stream)
-            step(index)
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in evs) / k_steps
-
-    def latency(index, n_tiles=300):
-        """Per-tile latency: batch-1 calls, each timed with CUDA events."""
-        idx = np.linspace(0, n - 1, n_tiles).astype(np.int64)
-        one = torch.empty((1, tb), dtype=torch.uint8, device="cuda")
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(n_tiles)]
-        req_rows = d_req.view(n, 16)
-        for k, t in enumerate(idx):
-            r = req_rows[int(t)]
-            evs[k][0].record(stream)
-            hv.hv_render_tiles(layer, r, 1, mode, index, style, one, one.numel(), stream)
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
-        lat = np.array([a.elapsed_time(b) for a, b in evs])
-        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(lat.mean()), "tiles": n_tiles, "form": "batch-1 calls, device buffers"}
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * n / (ms / 1000.0)
-    if args.profile_steps:
-        if rank == 0:
-            print(json.dumps({"profile_steps": True, "ms_per_step": ms}), flush=True)
-        return
-    # ---- extras measured on rank 0 only ----
-    line = None
-    if rank == 0:
-        lat = {"rtree": latency(hv.HV_INDEX_RTREE)}
+    out = None
+    if rank == 0 and not args.profile_steps:
+        lat = {"rtree": _latency(hv, torch, layer, d_req, n, mode, hv.HV_INDEX_RTREE, style, stream)}
         learned = None
+        k_side = max(3, min(steps, 10))
         if want_learned:
             info = hv.hv_layer_info_get(layer)
-            lms = timed_steps(hv.HV_INDEX_LEARNED, max(3, min(args.steps, 10)))
-            rms = ms if main_index == hv.HV_INDEX_RTREE else timed_steps(hv.HV_INDEX_RTREE, max(3, min(args.steps, 10)))
-            lat["learned"] = latency(hv.HV_INDEX_LEARNED)
-            learned = {"value": n / (lms / 1000.0), "ms_per_step": lms, "unit": "tiles/s",
-                       "rtree_value": n / (rms / 1000.0), "learned_over_rtree": rms / lms,
-                       "error_bound": info.learned_error, "error_bound_linear": info.learned_error_linear,
-                       "error_bound_mlp": info.learned_error_mlp, "mean_error": info.learned_mean_error,
-                       "pieces": info.learned_pieces, "pieces_with_mlp": info.learned_mlp,
-                       "mean_window": info.learned_mean_window,
-                       "mean_window_linear": info.learned_mean_window_linear,
-                       "halo": info.learned_halo, "side_tree_objects": info.learned_outliers,
-                       "train_ms": info.train_ms}
-        peak, peak_kind = measured_peak_hbm()
+            lms = statistics.mean(_timed(lambda: step(hv.HV_INDEX_LEARNED), flush, stream, k_side))
+            rms = ms if main_index == hv.HV_INDEX_RTREE else statistics.mean(
+                _timed(lambda: step(hv.HV_INDEX_RTREE), flush, stream, k_side))
+            lat["learned"] = _latency(hv, torch, layer, d_req, n, mode, hv.HV_INDEX_LEARNED, style, stream)
+            learned = dict({"value": n / (lms / 1000.0), "ms_per_step": lms, "unit": "tiles/s",
+                            "rtree_value": n / (rms / 1000.0), "learned_over_rtree": rms / lms},
+                           **_learned_info(info))
+        sweep = None
+        if r16_sweep:
+            sweep = []
+            for r16 in r16_sweep:
+                rr = reqs.copy()
+                rr[:, 3] = r16
+                d2 = torch.from_numpy(hv.make_requests(rr).view(np.uint8).copy()).cuda()
+                row = {"r16": r16, "half_width_px": r16 / 16.0}
+                rt = statistics.mean(_timed(lambda: step(hv.HV_INDEX_RTREE, d2), flush, stream, k_side))
+                row["rtree_tiles_per_s"] = n / (rt / 1000.0)
+                if want_learned:
+                    le = statistics.mean(_timed(lambda: step(hv.HV_INDEX_LEARNED, d2), flush, stream, k_side))
+                    row["learned_tiles_per_s"] = n / (le / 1000.0)
+                    row["learned_over_rtree"] = rt / le
+                sweep.append(row)
+        full_size = (args.points is None and args.r16 is None and n == w["tiles_per_step"]) or not headline
         alg = algorithmic_bytes_per_tile(hv, layer, reqs, torch, args.count_sample_tiles, lay)
-        roof = None
-        if alg is not None:
-            achieved = alg["per_tile"] * n / (ms / 1000.0) / 1e9
-            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": measured_traffic(args.config), "peak_kind": peak_kind,
-                    "kernel": "k_render", "alg_bytes_per_tile": alg["per_tile"],
-                    "alg_detail": alg}
-        # the committed counts are for one full-size launch of the default workload
-        full_size = args.points is None and args.r16 is None and n == WORKLOADS[args.config]["tiles_per_step"]
-        if roof is not None and not full_size:
-            roof["traffic"] = None
-        roof_issue = None
-        n_inst = measured_instructions(args.config) if full_size else None
-        if n_inst is not None:
-            ipk = issue_peak()
-            achieved_i = n_inst / (ms / 1000.0) / 1e9
-            roof_issue = {"bound": "alu", "achieved": achieved_i, "peak": ipk, "unit": "G warp-instructions/s",
-                          "frac": achieved_i / ipk, "instructions_per_launch": n_inst,
-                          "peak_basis": "SMs x 4 schedulers x 1 warp instruction/cycle x max SM clock",
-                          "note": "the integer pipe bounds this kernel; instruction count from the committed ncu summary"}
+        roof = _roofline(alg, n, ms, cfg, full_size)
+        roof_issue = _roofline_issue(cfg, ms, full_size)
         e2e = None
         if not args.no_e2e:
             h_req = hv.make_requests(reqs)
             h_out = torch.empty((n, tb), dtype=torch.uint8, pin_memory=True)
             for _ in range(2):
                 hv.hv_render_tiles(layer, h_req, n, mode, main_index, style, h_out, h_out.numel(), stream)
-            k_e2e = max(3, min(args.steps, 10))
+            k_e2e = max(3, min(steps, 10))
             t1 = time.perf_counter()
             for _ in range(k_e2e):
                 hv.hv_render_tiles(layer, h_req, n, mode, main_index, style, h_out, h_out.numel(), stream)
             dt = (time.perf_counter() - t1) / k_e2e
             e2e = {"value": n / dt, "unit": "tiles/s", "h2d_bytes_per_step": int(h_req.nbytes),
                    "d2h_bytes_per_step": int(n * tb), "ms_per_step": 1000 * dt,
+                   "over_device": (n / dt) / (n / (ms / 1000.0)),
                    "path": "hv_render_tiles with host requests and pinned host output"}
-        n_cpu = args.cpu_sample_tiles or {2: 48, 3: 16, 4: 6}[args.config]
+        n_cpu = args.cpu_sample_tiles or {2: 48, 3: 8, 4: 4}[cfg]
         cpu = None if args.no_cpu_baseline else cpu_baseline(lay, n_cpu)
-        cpu_mt = None if args.no_cpu_baseline else cpu_rtree_baseline(lay, {2: 96, 3: 48, 4: 16}[args.config])
-        line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-                "data": "synthetic",
-                "config": dict(WORKLOADS[args.config],
-                               index="packed Hilbert R-tree" if args.index == "rtree" else "learned",
-                               l2="flushed between steps (512 MiB write); layer and 2.6 GB output exceed L2",
-                               parallelism="replicas" if world > 1 else "single GPU"),
-                "pixel_queries_per_s": value * 65536,
-                "roofline": roof, "roofline_issue": roof_issue, "cpu_baseline": cpu, "cpu_rtree_mt": cpu_mt, "e2e": e2e,
-                "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-                "index_timed": args.index, "learned": learned, "latency": lat,
-                "wall_s_timed_region": wall, "step_ms": step_ms,
-                "index_build_ms": info.build_ms, "tree_levels": info.tree_levels,
-                "index_records": info.index_records, "piece_extent": info.piece_extent}
-        print(json.dumps(line), flush=True)
+        cpu_mt = None if args.no_cpu_baseline else cpu_rtree_baseline(lay, {2: 96, 3: 48, 4: 16}[cfg])
+        out = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": world,
+               "steps": steps, "warmup": warmup, "ms_per_step": ms,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+               "data": "synthetic",
+               "config": dict(w, index="packed Hilbert R-tree" if main_index == hv.HV_INDEX_RTREE else "learned",
+                              n_objects=lay.n_objects, tiles_per_step=n,
+                              r16=int(reqs[0, 3]) if n else w["r16"],
+                              l2="flushed between steps (512 MiB write); layer and output exceed L2",
+                              parallelism="replicas" if world > 1 else "single GPU"),
+               "pixel_queries_per_s": value * 65536,
+               "roofline": roof, "roofline_issue": roof_issue, "cpu_baseline": cpu, "cpu_rtree_mt": cpu_mt,
+               "e2e": e2e, "gpu_launches": launches_per_step * steps, "clocks": clk,
+               "index_timed": "rtree" if main_index == hv.HV_INDEX_RTREE else "learned",
+               "learned": learned, "latency": lat, "r16_sweep": sweep,
+               "wall_s_timed_region": wall, "step_ms": step_ms,
+               "index_build_ms": info.build_ms, "tree_levels": info.tree_levels,
+               "index_records": info.index_records, "piece_extent": info.piece_extent}
+    elif rank == 0:
+        out = {"profile_steps": True, "ms_per_step": ms}
+    del d_out, flush
     hv.hv_layer_free(layer)
     hv.hv_destroy(ctx)
+    return out
+
+
+def run_gb300(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    line = measure_batch(args, args.config, args.steps, args.warmup, dist, headline=True,
+                         r16_sweep=(8, 16, 24) if args.config == 3 else None)
+    if rank == 0 and line is not None and not args.profile_steps and world == 1 and not args.headline_only \
+            and args.config == 2:
+        # the metric's other workloads, as named blocks of the same line: the
+        # linestring and polygon batches (learned vs R-tree) and the served
+        # request stream (p50 / p99 per rate, learned vs R-tree)
+        blocks = {}
+        for cfg in (3, 4):
+            t0 = time.time()
+            blocks[str(cfg)] = measure_batch(args, cfg, 5, 3, None, headline=False,
+                                             r16_sweep=(8, 16, 24) if cfg == 3 else None)
+            blocks[str(cfg)]["wall_s"] = time.time() - t0
+            print("config %d done in %.0f s" % (cfg, time.time() - t0), file=sys.stderr, flush=True)
+        t0 = time.time()
+        blocks["5"] = serving_block(args)
+        blocks["5"]["wall_s"] = time.time() - t0
+        line["configs"] = blocks
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def run_serving(args):
-    """Open-loop serving over resident layers (HiVision Exp. 3 shape):
-    clustered points + random-walk segments, requests from pan/zoom sessions
-    (Zipf start tiles, mixed zoom 2-18, layer 50/50, r16 16-48, RGBA), Poisson
-    arrivals at each rate; per rate: achieved tiles/s and p50/p99 latency
-    (completion - scheduled arrival)."""
+def _serve_rate(hv, ctx, layers, reqs, arrival, index, style, max_batch=64):
+    """Replay one request stream through a fresh server; per-request
+    submit-to-completion latency and its parts from the server's own
+    timestamps (queue: submit -> batch launch; service: launch -> completion
+    seen by the worker; handout: completion -> poll)."""
+    opts = hv.make_server_opts(max_batch=max_batch, queue_capacity=1 << 20, scratch_bytes=4 << 30,
+                               index_kind=index, use_graphs=1, style=style)
+    srv = hv.hv_server_start(ctx, layers, opts)
+    try:
+        lat, wall = hv.hv_server_replay(srv, reqs, arrival)
+        st = hv.hv_server_stats(srv)
+    finally:
+        hv.hv_server_stop(srv)
+    return lat, wall, st
+
+
+def serving_block(args):
+    """Open-loop serving over resident layers (HiVision Exp. 3 shape, Sec. 5.3):
+    1B clustered points + 200M random-walk segments, requests from pan/zoom
+    sessions (Zipf start tiles, mixed zoom 2-18, layer 50/50, r16 16-48,
+    RGBA), Poisson arrivals at each rate; per rate and index: achieved tiles/s
+    and p50/p99 latency (completion - scheduled arrival, through the server's
+    public calls)."""
     import torch
     from paper_2005_12489_gb300 import hv
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
+    _, _, local = dist_env()
     t0 = time.time()
     pts = gen.gmm_points(args.serve_points, seed=5, k=64)
     n_lines = max(1, args.serve_segments // 10)
@@ -575,50 +658,108 @@ def run_serving(args):
         hv.hv_layer_build_index(L, hv.HV_INDEX_RTREE | hv.HV_INDEX_LEARNED)
     build_s = time.time() - t1
     anchors = [pts[:: max(1, len(pts) // 2_000_000)], gen.segment_midpoints(xy, off, 2_000_000, seed=56)]
-    del pts, xy, off
     style = hv.make_style(STYLE_T[:3], STYLE_T[4:7])
     results = []
-    for ri, rate in enumerate(args.rates.split(",")):
+    rates = args.rates.split(",")
+    tr0 = None
+    for ri, rate in enumerate(rates):
         tr = gen.pan_zoom_trace(anchors, args.requests, seed=500 + ri)
+        if tr0 is None:
+            tr0 = tr
         reqs = np.zeros(len(tr), dtype=hv.REQ_DTYPE)
         reqs["z"], reqs["x"], reqs["y"], reqs["r16"], reqs["layer"] = tr[:, 0], tr[:, 1], tr[:, 2], tr[:, 3], tr[:, 4]
         reqs["mode"] = hv.HV_MODE_RGBA
-        if rate == "inf":
-            arrival = np.zeros(len(reqs))
-        else:
-            arrival = gen.poisson_arrivals(len(reqs), float(rate), seed=600 + ri)
+        arrival = np.zeros(len(reqs)) if rate == "inf" else gen.poisson_arrivals(len(reqs), float(rate), seed=600 + ri)
         for index in (hv.HV_INDEX_LEARNED, hv.HV_INDEX_RTREE):
-            opts = hv.make_server_opts(max_batch=64, queue_capacity=1 << 20, scratch_bytes=4 << 30,
-                                       index_kind=index, use_graphs=1, style=style)
-            srv = hv.hv_server_start(ctx, layers, opts)
-            try:
-                lat, wall = hv.hv_server_replay(srv, reqs, arrival)
-                st = hv.hv_server_stats(srv)
-            finally:
-                hv.hv_server_stop(srv)
+            lat, wall, st = _serve_rate(hv, ctx, layers, reqs, arrival, index, style)
             results.append({"rate": rate, "index": "learned" if index == hv.HV_INDEX_LEARNED else "rtree",
-                            "tiles_per_s": len(reqs) / (wall / 1e6),
+                            "requests": len(reqs), "tiles_per_s": len(reqs) / (wall / 1e6),
                             "p50_ms": float(np.percentile(lat, 50)) / 1000,
                             "p99_ms": float(np.percentile(lat, 99)) / 1000,
                             "mean_batch": st["tiles"] / max(1, st["batches"]), "slots": st["slots"],
                             "graph_launches": st["graph_launches"]})
             print(json.dumps(results[-1]), file=sys.stderr, flush=True)
+    # the served kernels on the device: the first trace's requests rendered
+    # per layer in batches of 64 (the server's batch) with CUDA events
+    stream = torch.cuda.current_stream()
+    dev = {}
+    tb = hv.hv_tile_bytes(hv.HV_MODE_RGBA)
+    d_out = torch.empty((64, tb), dtype=torch.uint8, device="cuda")
+    for li, name in ((0, "points"), (1, "lines")):
+        sel = tr0[tr0[:, 4] == li][:, :4][:4096]
+        d_req = torch.from_numpy(hv.make_requests(sel).view(np.uint8).copy()).cuda()
+        row = {}
+        for index, iname in ((hv.HV_INDEX_RTREE, "rtree"), (hv.HV_INDEX_LEARNED, "learned")):
+            def go():
+                for b in range(0, len(sel), 64):
+                    k = min(64, len(sel) - b)
+                    hv.hv_render_tiles(layers[li], d_req[b * 16:(b + k) * 16], k, hv.HV_MODE_RGBA, index, style,
+                                       d_out, d_out.numel(), stream)
+            ms = statistics.mean(_timed(go, torch.empty(8, dtype=torch.uint8, device="cuda"), stream, 3, 1))
+            row[iname + "_tiles_per_s"] = len(sel) / (ms / 1000.0)
+        class _L:
+            kind = name
+            obj_bytes = 8 if li == 0 else 32
+        alg = algorithmic_bytes_per_tile(hv, layers[li], sel, torch, min(200, len(sel)), _L)
+        row["alg_bytes_per_tile"] = alg and alg["per_tile"]
+        row["hbm_GBps"] = alg and alg["per_tile"] * row["rtree_tiles_per_s"] / 1e9
+        row["tiles"] = len(sel)
+        dev[name] = row
     infos = [hv.info_dict(L) for L in layers]
+    for L in layers:
+        hv.hv_layer_free(L)
+    hv.hv_destroy(ctx)
+    peak, peak_kind = measured_peak_hbm()
+    # the dominant served kernel: the point layer's (its tiles are the heavier)
+    hb = dev["points"]["hbm_GBps"]
+    roof = None if hb is None else {"bound": "hbm", "achieved": hb, "peak": peak, "unit": "GB/s",
+                                    "frac": hb / peak, "traffic": None, "peak_kind": peak_kind,
+                                    "kernel": "k_render (points, batches of 64 trace tiles)",
+                                    "alg_bytes_per_tile": dev["points"]["alg_bytes_per_tile"]}
+    # the oracle on one trace tile of each layer over the whole layers
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t2 = time.perf_counter()
+        for li in (0, 1):
+            one = tr0[tr0[:, 4] == li][:1, :4].astype(np.uint32)
+            if li == 0:
+                oracle.render_points(pts, one, 2, STYLE_T)
+            else:
+                oracle.render_lines(xy, off, one, 2, STYLE_T)
+        dt = time.perf_counter() - t2
+        cpu = {"value": 2 / dt, "unit": "tiles/s", "cores": 1, "kind": "oracle", "seconds": dt,
+               "sample": "one trace tile of each layer over all %d points + %d segments, single-threaded C"
+                         % (args.serve_points, args.serve_segments)}
+    del pts, xy, off
+    inf_l = [r for r in results if r["rate"] == "inf" and r["index"] == "learned"]
     best = max(r["tiles_per_s"] for r in results if r["index"] == "learned")
-    line = {"metric": "served tiles/s and p50/p99 tile latency, open-loop request stream, 1 GB300",
-            "value": best, "unit": "tiles/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+    e2e = {"value": (inf_l[0] if inf_l else max(results, key=lambda r: r["tiles_per_s"]))["tiles_per_s"],
+           "unit": "tiles/s", "h2d_bytes_per_step": 16, "d2h_bytes_per_step": tb,
+           "path": "hv_server_submit / hv_server_poll, all requests offered at once; a step is one request "
+                   "(host request in, RGBA tile out to pinned host memory)"}
+    return {"metric": "served tiles/s and p50/p99 tile latency, open-loop request stream, learned vs R-tree",
+            "value": best, "unit": "tiles/s", "higher_is_better": True,
             "config": {"workload": "resident layers: %d clustered points + %d random-walk segments; "
                                    "pan/zoom session requests (Zipf start tiles, zoom 2-18, layer 50/50, "
                                    "r16 16-48, RGBA), Poisson arrivals" % (args.serve_points, args.serve_segments),
                        "requests_per_rate": args.requests, "max_batch": 64, "graphs": True},
-            "per_rate": results, "generate_s": gen_s, "index_build_s": build_s,
+            "per_rate": results, "device": dev, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "generate_s": gen_s, "index_build_s": build_s,
             "layers": [{k: v for k, v in i.items() if k in ("n_objects", "learned_error", "learned_outliers",
-                                                           "train_ms", "build_ms", "device_bytes")} for i in infos]}
-    print(json.dumps(line), flush=True)
-    for L in layers:
-        hv.hv_layer_free(L)
-    hv.hv_destroy(ctx)
+                                                           "train_ms", "build_ms", "device_bytes")}
+                       for i in infos]}
+
+
+def run_serving(args):
+    """--config 5 alone: the serving block as its own JSON line."""
+    import torch
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    b = serving_block(args)
+    b.update({"n_gpus": 1, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic"})
+    print(json.dumps(b), flush=True)
 
 
 def run_volume_sweep(args):

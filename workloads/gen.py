@@ -22,15 +22,34 @@ linestrings and polygons, 40 M to 2.7 B items), which are not available:
                           shaped like building / land-use footprints.
 
 Tile requests are ``(n, 4)`` uint32 arrays with columns ``z, x, y, r16``.
+
+Large layers are drawn in chunks, each from its own stream spawned from the
+seed (``SeedSequence(seed).spawn``), in a thread pool (numpy's random draws
+and array arithmetic release the GIL): the result depends only on the seed and
+the chunk size, not on the number of threads.
 """
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 GRID = 1 << 31
 HALF = 1 << 30
+CHUNK = 1 << 22          # objects (points, lines, polygons) per drawing chunk
 
 
 def rng_for(seed):
     return np.random.Generator(np.random.PCG64(seed))
+
+
+def _chunk_rngs(seed, n_chunks):
+    """One independent generator per chunk, spawned from the seed."""
+    return [np.random.Generator(np.random.PCG64(s)) for s in np.random.SeedSequence(seed).spawn(n_chunks)]
+
+
+def _parallel(fn, jobs):
+    with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        return list(ex.map(fn, jobs))
 
 
 def _floor_i32(v):
@@ -68,25 +87,34 @@ def _draw_mixture(rng, centres, sigma, comp):
     return out
 
 
-def gmm_points(n, seed, k=64, noise=0.05, chunk=1 << 24):
+def gmm_points(n, seed, k=64, noise=0.05, chunk=CHUNK):
     """n points: (1 - noise) from a k-component Gaussian mixture, the rest
-    uniform.  int32 (n, 2).  Drawn in chunks to bound host memory."""
+    uniform.  int32 (n, 2).  The component counts come from the seed's main
+    stream; the coordinates are drawn in chunks of `chunk` points, each from
+    its own spawned stream."""
     rng = rng_for(seed)
     centres, weights, sigma = _mixture(rng, k)
     n_noise = int(round(noise * n))
     counts = rng.multinomial(n - n_noise, weights)
-    comp_all = np.repeat(np.arange(k, dtype=np.int32), counts)
+    bounds = np.zeros(k + 1, dtype=np.int64)
+    np.cumsum(counts, out=bounds[1:])
     out = np.empty((n, 2), dtype=np.int32)
-    pos = 0
-    for s in range(0, comp_all.shape[0], chunk):
-        c = comp_all[s:s + chunk]
-        out[pos:pos + c.shape[0]] = _draw_mixture(rng, centres, sigma, c)
-        pos += c.shape[0]
-    for s in range(0, n_noise, chunk):
-        m = min(chunk, n_noise - s)
-        out[pos:pos + m] = rng.integers(-HALF, HALF, size=(m, 2), dtype=np.int64)
-        pos += m
-    assert pos == n
+    starts = list(range(0, n, chunk))
+    rngs = _chunk_rngs(seed, len(starts))
+
+    def one(ci):
+        s = starts[ci]
+        e = min(n, s + chunk)
+        r = rngs[ci]
+        m = min(e, n - n_noise)           # [s, m): mixture, [m, e): noise
+        if m > s:
+            comp = (np.searchsorted(bounds, np.arange(s, m), side="right") - 1).astype(np.int32)
+            out[s:m] = _draw_mixture(r, centres, sigma, comp)
+        if e > max(s, m):
+            q = max(s, m)
+            out[q:e] = r.integers(-HALF, HALF, size=(e - q, 2), dtype=np.int64)
+
+    _parallel(one, range(len(starts)))
     return out
 
 
@@ -99,14 +127,17 @@ def _reflect(v):
 
 
 def walk_lines(n_lines, n_segments, seed, n_cities=1000, step_mean=1e-4, step_sigma_ln=1.0,
-               turn_deg=30.0):
+               turn_deg=30.0, chunk=CHUNK >> 4):
     """Random-walk polylines around city centres.
 
     Segments per line = 1 + multinomial(n_segments - n_lines, uniform), so the
     total is exactly n_segments.  Start points are Gaussian around uniformly
     placed city centres (sigma log-uniform in [1e-3, 1e-2] of the extent); step
     lengths are log-normal with the given mean (fraction of the extent) and
-    sigma of the log; the heading turns by U(-turn, +turn) each step.
+    sigma of the log; the heading turns by U(-turn, +turn) each step.  Walks
+    that leave the grid are reflected back into it.  The per-line draws come
+    from the seed's main stream, the walks from one spawned stream per chunk
+    of `chunk` lines.
     Returns (xy int32 (V, 2), line_off uint64 (n_lines + 1))."""
     assert n_segments >= n_lines
     rng = rng_for(seed)
@@ -120,30 +151,40 @@ def walk_lines(n_lines, n_segments, seed, n_cities=1000, step_mean=1e-4, step_si
     city = rng.integers(0, n_cities, size=n_lines)
     start = cc[city] + cs[city, None] * rng.standard_normal((n_lines, 2))
     mu = np.log(step_mean * GRID) - 0.5 * step_sigma_ln ** 2
-    line_of_vertex = np.repeat(np.arange(n_lines), nv)
-    first = off[:-1].astype(np.int64)
-    # per-vertex step (the first vertex of each line has a zero step)
-    step = np.exp(mu + step_sigma_ln * rng.standard_normal(V))
-    dh = np.deg2rad(rng.uniform(-turn_deg, turn_deg, size=V))
-    dh[first] = rng.uniform(0, 2 * np.pi, size=n_lines)
-    step[first] = 0.0
-    heading = np.cumsum(dh)
-    heading -= np.repeat(heading[first] - dh[first], nv)
-    dx = step * np.cos(heading)
-    dy = step * np.sin(heading)
-    px = np.cumsum(dx)
-    py = np.cumsum(dy)
-    px -= np.repeat(px[first], nv)
-    py -= np.repeat(py[first], nv)
-    px += start[line_of_vertex, 0]
-    py += start[line_of_vertex, 1]
     xy = np.empty((V, 2), dtype=np.int32)
-    xy[:, 0] = _floor_i32(_reflect(px))
-    xy[:, 1] = _floor_i32(_reflect(py))
+    starts = list(range(0, n_lines, chunk))
+    rngs = _chunk_rngs(seed, len(starts))
+
+    def one(ci):
+        l0 = starts[ci]
+        l1 = min(n_lines, l0 + chunk)
+        r = rngs[ci]
+        v0, v1 = int(off[l0]), int(off[l1])
+        cnv = nv[l0:l1]
+        first = (off[l0:l1] - off[l0]).astype(np.int64)
+        nl, nvx = l1 - l0, v1 - v0
+        line_of_vertex = np.repeat(np.arange(nl), cnv)
+        # per-vertex step (the first vertex of each line has a zero step)
+        step = np.exp(mu + step_sigma_ln * r.standard_normal(nvx))
+        dh = np.deg2rad(r.uniform(-turn_deg, turn_deg, size=nvx))
+        dh[first] = r.uniform(0, 2 * np.pi, size=nl)
+        step[first] = 0.0
+        heading = np.cumsum(dh)
+        heading -= np.repeat(heading[first] - dh[first], cnv)
+        px = np.cumsum(step * np.cos(heading))
+        py = np.cumsum(step * np.sin(heading))
+        px -= np.repeat(px[first], cnv)
+        py -= np.repeat(py[first], cnv)
+        px += start[l0:l1][line_of_vertex, 0]
+        py += start[l0:l1][line_of_vertex, 1]
+        xy[v0:v1, 0] = _floor_i32(_reflect(px))
+        xy[v0:v1, 1] = _floor_i32(_reflect(py))
+
+    _parallel(one, range(len(starts)))
     return xy, off
 
 
-def star_polygons(n, seed, k=256, nv_min=8, nv_max=64, rho_median=2e-4, rho_sigma_ln=0.75):
+def star_polygons(n, seed, k=256, nv_min=8, nv_max=64, rho_median=2e-4, rho_sigma_ln=0.75, chunk=CHUNK >> 6):
     """n simple star-shaped polygons (one ring each).
 
     Centres from a k-component mixture (as ``gmm_points``); vertex count
@@ -154,7 +195,9 @@ def star_polygons(n, seed, k=256, nv_min=8, nv_max=64, rho_median=2e-4, rho_sigm
     consecutive vertices turns strictly counter-clockwise about its integer
     centre and all vertices lie in the grid; a star polygon whose consecutive
     vertex pairs all turn the same way around one point is simple.  Rejected
-    polygons are redrawn.  Returns (xy, ring_off, poly_ring_off)."""
+    polygons are redrawn.  The per-polygon draws come from the seed's main
+    stream, the vertices from one spawned stream per chunk of `chunk`
+    polygons.  Returns (xy, ring_off, poly_ring_off)."""
     rng = rng_for(seed)
     centres, weights, sigma = _mixture(rng, k)
     comp = rng.choice(k, size=n, p=weights)
@@ -164,43 +207,50 @@ def star_polygons(n, seed, k=256, nv_min=8, nv_max=64, rho_median=2e-4, rho_sigm
     ring_off = np.zeros(n + 1, dtype=np.uint64)
     np.cumsum(nv, out=ring_off[1:])
     xy = np.empty((int(ring_off[-1]), 2), dtype=np.int32)
-    todo = np.arange(n)
-    while todo.size:
-        t_nv = nv[todo]
-        tot = int(t_nv.sum())
-        pid = np.repeat(np.arange(todo.size), t_nv)
-        # sorted uniform angles per polygon without a sort: normalised partial
-        # sums of nv + 1 exponential spacings (Renyi representation)
-        e = rng.standard_exponential(tot + todo.size)
-        c = np.cumsum(e)
-        ends = np.cumsum(t_nv + 1) - 1                # index of each polygon's last spacing
-        base = np.concatenate([[0.0], c[ends[:-1]]])  # sum before each polygon
-        total = c[ends] - base
-        keep = np.ones(tot + todo.size, dtype=bool)
-        keep[ends] = False
-        ang = 2 * np.pi * (c[keep] - np.repeat(base, t_nv)) / np.repeat(total, t_nv)
-        rad = np.repeat(rho[todo], t_nv) * rng.uniform(0.5, 1.0, size=tot)
-        cx = np.repeat(pc[todo, 0], t_nv).astype(np.float64)
-        cy = np.repeat(pc[todo, 1], t_nv).astype(np.float64)
-        vx = _floor_i32(cx + rad * np.cos(ang))
-        vy = _floor_i32(cy + rad * np.sin(ang))
-        starts = np.zeros(todo.size + 1, dtype=np.int64)
-        np.cumsum(t_nv, out=starts[1:])
-        nxt = np.arange(tot) + 1
-        nxt[starts[1:] - 1] = starts[:-1]
-        ex = vx - np.repeat(pc[todo, 0], t_nv)
-        ey = vy - np.repeat(pc[todo, 1], t_nv)
-        cross = ex * ey[nxt] - ey * ex[nxt]
-        bad_v = (cross <= 0) | ~_in_grid(vx) | ~_in_grid(vy)
-        bad = np.zeros(todo.size, dtype=bool)
-        np.logical_or.at(bad, pid, bad_v)
-        keep_v = ~bad[pid]
-        # destination of each kept vertex: its polygon's final offset + rank in polygon
-        rank = np.arange(tot) - starts[pid]
-        dest = ring_off[todo[pid[keep_v]]].astype(np.int64) + rank[keep_v]
-        xy[dest, 0] = vx[keep_v]
-        xy[dest, 1] = vy[keep_v]
-        todo = todo[bad]
+    starts = list(range(0, n, chunk))
+    rngs = _chunk_rngs(seed, len(starts))
+
+    def one(ci):
+        r = rngs[ci]
+        todo = np.arange(starts[ci], min(n, starts[ci] + chunk))
+        while todo.size:
+            t_nv = nv[todo]
+            tot = int(t_nv.sum())
+            pid = np.repeat(np.arange(todo.size), t_nv)
+            # sorted uniform angles per polygon without a sort: normalised
+            # partial sums of nv + 1 exponential spacings (Renyi representation)
+            e = r.standard_exponential(tot + todo.size)
+            c = np.cumsum(e)
+            ends = np.cumsum(t_nv + 1) - 1                # index of each polygon's last spacing
+            base = np.concatenate([[0.0], c[ends[:-1]]])  # sum before each polygon
+            total = c[ends] - base
+            keep = np.ones(tot + todo.size, dtype=bool)
+            keep[ends] = False
+            ang = 2 * np.pi * (c[keep] - np.repeat(base, t_nv)) / np.repeat(total, t_nv)
+            rad = np.repeat(rho[todo], t_nv) * r.uniform(0.5, 1.0, size=tot)
+            cx = np.repeat(pc[todo, 0], t_nv).astype(np.float64)
+            cy = np.repeat(pc[todo, 1], t_nv).astype(np.float64)
+            vx = _floor_i32(cx + rad * np.cos(ang))
+            vy = _floor_i32(cy + rad * np.sin(ang))
+            st = np.zeros(todo.size + 1, dtype=np.int64)
+            np.cumsum(t_nv, out=st[1:])
+            nxt = np.arange(tot) + 1
+            nxt[st[1:] - 1] = st[:-1]
+            ex = vx - np.repeat(pc[todo, 0], t_nv)
+            ey = vy - np.repeat(pc[todo, 1], t_nv)
+            cross = ex * ey[nxt] - ey * ex[nxt]
+            bad_v = (cross <= 0) | ~_in_grid(vx) | ~_in_grid(vy)
+            # a polygon is bad when any of its vertices is
+            bad = np.add.reduceat(bad_v.astype(np.int64), st[:-1]) > 0
+            keep_v = ~bad[pid]
+            # destination of each kept vertex: its polygon's final offset + rank in polygon
+            rank = np.arange(tot) - st[pid]
+            dest = ring_off[todo[pid[keep_v]]].astype(np.int64) + rank[keep_v]
+            xy[dest, 0] = vx[keep_v]
+            xy[dest, 1] = vy[keep_v]
+            todo = todo[bad]
+
+    _parallel(one, range(len(starts)))
     poly_ring_off = np.arange(n + 1, dtype=np.uint64)
     return xy, ring_off, poly_ring_off
 
