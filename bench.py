@@ -413,6 +413,31 @@ def _latency(hv, torch, layer, d_req, n, mode, index, style, stream, n_tiles=300
             "mean_ms": float(lat.mean()), "tiles": n_tiles, "form": "batch-1 calls, device buffers"}
 
 
+def phase_profile(hv, torch, layer, d_req, n, mode, index, style, d_out, kind):
+    """Where the render kernel's time goes: one launch of the instrumented
+    instantiation (hv_render_tiles_phases), as shares of the launch's
+    warp-cycles, and visit counts per tile.  Polygon layers report the outline
+    and the fill launch apart."""
+    cnt = hv.HV_PHASE_COUNT * (2 if kind == "polygons" else 1)
+    ph = torch.zeros(cnt, dtype=torch.int64, device="cuda")
+    hv.hv_render_tiles_phases(layer, d_req, n, mode, index, style, d_out, d_out.numel(), ph)
+    torch.cuda.synchronize()
+    v = ph.cpu().numpy().astype(np.float64)
+    parts = {}
+    for k, name in enumerate(["outline", "fill"] if kind == "polygons" else ["render"]):
+        c = v[hv.HV_PHASE_COUNT * k:hv.HV_PHASE_COUNT * (k + 1)]
+        tot = max(c[0], 1.0)
+        busy, leaf, desc = c[5], c[6], c[7]
+        parts[name] = {
+            "share": {"prologue": c[1] / tot, "cull": c[2] / tot, "bin": c[3] / tot,
+                      "frontier_scan": (busy - desc) / tot, "node_tests": (desc - leaf) / tot,
+                      "leaf_visits": leaf / tot, "blocks_waiting": (c[4] - busy) / tot, "encode": c[8] / tot},
+            "per_tile": {"blocks": c[10] / n, "leaf_visits": c[11] / n, "node_visits": c[12] / n,
+                         "frontier_tests": c[13] / n},
+            "warp_cycles_per_tile": tot / n}
+    return parts
+
+
 def _learned_info(info):
     return {"error_bound": info.learned_error, "error_bound_linear": info.learned_error_linear,
             "error_bound_mlp": info.learned_error_mlp, "mean_error": info.learned_mean_error,
@@ -539,6 +564,10 @@ def measure_batch(args, cfg, steps, warmup, dist=None, headline=False, r16_sweep
                     row["learned_tiles_per_s"] = n / (le / 1000.0)
                     row["learned_over_rtree"] = rt / le
                 sweep.append(row)
+        phases = {"rtree": phase_profile(hv, torch, layer, d_req, n, mode, hv.HV_INDEX_RTREE, style, d_out, lay.kind)}
+        if want_learned:
+            phases["learned"] = phase_profile(hv, torch, layer, d_req, n, mode, hv.HV_INDEX_LEARNED, style, d_out,
+                                              lay.kind)
         full_size = (args.points is None and args.r16 is None and n == w["tiles_per_step"]) or not headline
         alg = algorithmic_bytes_per_tile(hv, layer, reqs, torch, args.count_sample_tiles, lay)
         roof = _roofline(alg, n, ms, cfg, full_size)
@@ -574,7 +603,7 @@ def measure_batch(args, cfg, steps, warmup, dist=None, headline=False, r16_sweep
                "roofline": roof, "roofline_issue": roof_issue, "cpu_baseline": cpu, "cpu_rtree_mt": cpu_mt,
                "e2e": e2e, "gpu_launches": launches_per_step * steps, "clocks": clk,
                "index_timed": "rtree" if main_index == hv.HV_INDEX_RTREE else "learned",
-               "learned": learned, "latency": lat, "r16_sweep": sweep,
+               "learned": learned, "latency": lat, "r16_sweep": sweep, "phases": phases,
                "wall_s_timed_region": wall, "step_ms": step_ms,
                "index_build_ms": info.build_ms, "tree_levels": info.tree_levels,
                "index_records": info.index_records, "piece_extent": info.piece_extent}

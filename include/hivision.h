@@ -254,6 +254,38 @@ int hv_render_tiles_counted(hv_layer* layer, const hv_tile_req* reqs, uint32_t n
                             int index_kind, const hv_style* style, void* out, uint64_t out_bytes,
                             int64_t* log, uint64_t log_cap, int64_t* log_count, void* stream);
 
+/* Phase profile counters of hv_render_tiles_phases (indices into its array;
+ * a polygon layer's fill launch uses a second set at HV_PHASE_COUNT + i). */
+enum {
+    HV_PHASE_TOTAL = 0,       /* warp-cycles of the launch (CTA lifetimes x warps) */
+    HV_PHASE_PROLOGUE,        /* request decode, result init (fill: outline decode) */
+    HV_PHASE_CULL,            /* tile cull of the strip: R-tree or learned lookup */
+    HV_PHASE_BIN,             /* binning the frontier by block column */
+    HV_PHASE_BLOCKS_CTA,      /* the pixel-block phase, CTA time x warps */
+    HV_PHASE_BLOCKS_WARP,     /* ... of which warps were busy (rest: waiting) */
+    HV_PHASE_LEAF,            /* ... of which in leaf visits (exact predicates) */
+    HV_PHASE_DESCEND,         /* ... of which below the frontier: node tests and
+                                 leaf visits (the rest of the busy time is the
+                                 blocks' scans of the frontier) */
+    HV_PHASE_ENCODE,          /* output encode */
+    HV_PHASE_CTAS,            /* counts: CTAs, */
+    HV_PHASE_BLOCK_COUNT,     /*   8 x 4 pixel blocks, */
+    HV_PHASE_LEAF_VISITS,     /*   leaf visits, */
+    HV_PHASE_NODE_VISITS,     /*   inner-node visits in descents, */
+    HV_PHASE_FRONTIER_TESTS,  /*   frontier entries tested by blocks */
+    HV_PHASE_COUNT = 16
+};
+
+/* Instrumented hv_render_tiles for measurement (not for production use):
+ * the same tiles, rendered by an instrumented copy of the kernel that times
+ * its phases with the SM clock and adds the warp-cycles of each phase (and a
+ * few counts) to `phases` (device memory, HV_PHASE_COUNT entries, or 2 x
+ * HV_PHASE_COUNT for polygon layers; the caller zeroes them).  All buffers are
+ * device memory.  Used to find where the render kernel's time goes. */
+int hv_render_tiles_phases(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode,
+                           int index_kind, const hv_style* style, void* out, uint64_t out_bytes,
+                           uint64_t* phases, void* stream);
+
 /* Number of kernels hv_render_tiles launches per call (for launch accounting):
  * 1 for point and linestring layers, 2 for polygon layers (outline, then
  * fill); a call with host buffers launches that many per chunk of tiles. */

@@ -494,6 +494,22 @@ int hv_render_tiles_counted(hv_layer* layer, const hv_tile_req* reqs, uint32_t n
     return launch_render(L, reqs, n, mode, index_kind, style, (uint8_t*)out, (cudaStream_t)stream, &rl);
 }
 
+int hv_render_tiles_phases(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode, int index_kind,
+                           const hv_style* style, void* out, uint64_t out_bytes, uint64_t* phases, void* stream) {
+    if (!layer || !reqs || !out || !phases) { set_error("hv_render_tiles_phases: NULL argument"); return HV_EINVAL; }
+    Layer* L = (Layer*)layer;
+    uint64_t tb = hv_tile_bytes(mode);
+    if (tb == 0 || out_bytes < (uint64_t)n * tb) { set_error("hv_render_tiles_phases: bad mode or size"); return HV_EINVAL; }
+    if (!(L->indexes & index_kind)) { set_error("hv_render_tiles_phases: index not built"); return HV_ESTATE; }
+    if (!is_device_ptr(reqs) || !is_device_ptr(out) || !is_device_ptr(phases)) {
+        set_error("hv_render_tiles_phases: all buffers must be device memory");
+        return HV_EINVAL;
+    }
+    HV_CUDA(cudaSetDevice(L->ctx->device));
+    RenderLog rl{nullptr, 0, nullptr, phases};
+    return launch_render(L, reqs, n, mode, index_kind, style, (uint8_t*)out, (cudaStream_t)stream, &rl);
+}
+
 int hv_layer_take_status(hv_layer* layer, void* stream, uint32_t* status) {
     if (!layer || !status) { set_error("hv_layer_take_status: NULL argument"); return HV_EINVAL; }
     Layer* L = (Layer*)layer;

@@ -157,6 +157,7 @@ struct RenderLog {
     int64_t* log;
     uint64_t cap;
     int64_t* count;
+    uint64_t* phases = nullptr;   // phase profile counters (instrumented launch)
 };
 int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int index_kind,
                   const hv_style* style, uint8_t* d_out, cudaStream_t stream,

@@ -90,7 +90,25 @@ struct Params {
     unsigned long long* log;
     unsigned long long log_cap;
     unsigned long long* log_n;
+    // phase profile (instrumented instantiation only): HV_PHASE_* counters
+    unsigned long long* phases;
 };
+
+// Phase profile.  The instrumented instantiation (kProf) times the phases of
+// every CTA with clock64() and adds them up over the launch, in warp-cycles:
+// CTA-wide phases (one thread times them, every warp takes part) count their
+// cycles times the warps of the CTA; block work counts each warp's own
+// cycles.  The indices are the HV_PHASE_* values of the C header.
+enum {
+    kPTotal = 0, kPPrologue, kPCull, kPBin, kPBlocksCta, kPBlocksWarp, kPLeaf, kPDescend, kPEncode,
+    kPCtas, kPBlocks, kPLeafVisits, kPNodeVisits, kPFrontierEntries, kPN = 16
+};
+
+template <bool kProf>
+__device__ __forceinline__ long long tick() {
+    if constexpr (kProf) return clock64();
+    return 0;
+}
 
 // kinds of logged reads
 constexpr uint32_t kLogNode = 0, kLogLeaf = 1, kLogPolyNode = 2, kLogPolyLeaf = 3, kLogPoly = 4;
@@ -127,7 +145,21 @@ struct Smem {
     int bucket_cur[kBlocksX];
     int binned;
     int f_count, f_level, f_buf, next_count, next_block;
+    unsigned long long prof[kPN];   // phase profile of the CTA (kProf only)
 };
+
+// Add the cycles since t0 (or a count) to a phase counter of the CTA (one
+// lane per warp).
+template <bool kProf>
+__device__ __forceinline__ void prof_add(Smem& sm, int k, unsigned long long v, int lane) {
+    if constexpr (kProf) {
+        if (lane == 0) atomicAdd(&sm.prof[k], v);
+    }
+}
+template <bool kProf>
+__device__ __forceinline__ void prof_since(Smem& sm, int k, long long t0, int lane) {
+    if constexpr (kProf) prof_add<kProf>(sm, k, (unsigned long long)(clock64() - t0), lane);
+}
 
 // Where a traversal reads its objects: a tree's sorted objects (with polygon
 // ids for polygon boxes) and the per-level node bases in shared memory.
@@ -536,7 +568,7 @@ __device__ __forceinline__ uint32_t child_hits(const Params& p, bool fill, const
 // keeps, per level, the node whose children are being visited, the children
 // still to visit, and each child's lane reach (re-tested against the
 // shrinking undecided set before every visit).
-template <class V>
+template <class V, bool kProf>
 __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, uint32_t node, Lane& s,
                         int lane, int warp) {
     uint32_t* stk_node = sm.stk_node[warp];
@@ -548,6 +580,7 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
     }
     uint32_t m0 = child_hits(p, V::kFill, src, src.lvl[lvl] + (uint64_t)node * 128, s, lane,
                              sm.lanemask[warp][lvl]);
+    prof_add<kProf>(sm, kPNodeVisits, 1, lane);
     if (s.U == 0) return;
     stk_node[lvl] = node;
     stk_mask[lvl] = m0;
@@ -566,7 +599,10 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
         stk_mask[lvl] = m & (m - 1);
         __syncwarp();
         if (lvl == 1) {
+            const long long t0 = tick<kProf>();
             V::visit(p, src, child, s, lane);
+            prof_since<kProf>(sm, kPLeaf, t0, lane);
+            prof_add<kProf>(sm, kPLeafVisits, 1, lane);
             if (s.U == 0) return;
         } else {
             if (child >= src.lvl_n[lvl - 1]) {
@@ -576,6 +612,7 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
             lvl--;
             uint32_t hm = child_hits(p, V::kFill, src, src.lvl[lvl] + (uint64_t)child * 128, s, lane,
                                      sm.lanemask[warp][lvl]);
+            prof_add<kProf>(sm, kPNodeVisits, 1, lane);
             if (s.U == 0) return;
             stk_node[lvl] = child;
             stk_mask[lvl] = hm;
@@ -815,10 +852,11 @@ __device__ void bin_frontier(Smem& sm, int32_t X0, int L, int32_t reach, int tid
 
 // Process every pixel block of the strip: against the culled frontier (R-tree)
 // or through the learned lookup.
-template <class V>
+template <class V, bool kProf>
 __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src& side, int side_top, int32_t X0,
                             int32_t Y0, int strip, int z, int32_t R, bool mask_mode, int tid) {
     int lane = tid & 31, warp = tid >> 5;
+    const long long t_active = tick<kProf>();
     const int L = 23 - z;
     const int32_t ps = 1 << L;
     const int f_count = sm.f_count, f_level = sm.f_level, fb = sm.f_buf;
@@ -836,6 +874,7 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         if (lane == 0) blk = atomicAdd(&sm.next_block, 1);
         blk = __shfl_sync(kFull, blk, 0);
         if (blk >= kBlocksX * (p.rows / kBH)) break;
+        prof_add<kProf>(sm, kPBlocks, 1, lane);
         int bx = blk % kBlocksX, by = blk / kBlocksX;
         int i = bx * kBW + (lane & 7);
         int jl = by * kBH + (lane >> 3);
@@ -886,22 +925,32 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                     }
                 }
                 uint32_t mm = __ballot_sync(kFull, reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
+                prof_add<kProf>(sm, kPFrontierEntries, (unsigned long long)min(32, lcnt - c0), lane);
                 while (mm) {
                     int k = __ffs(mm) - 1;
                     mm &= mm - 1;
                     uint32_t id = sm.fid[fb][__shfl_sync(kFull, e, k)];
+                    const long long t0 = tick<kProf>();
                     if (f_level == 0) {
                         V::visit(p, src, id, s, lane);
+                        prof_since<kProf>(sm, kPLeaf, t0, lane);
+                        prof_add<kProf>(sm, kPLeafVisits, 1, lane);
                     } else {
-                        descend<V>(p, sm, src, f_level, id, s, lane, warp);
+                        descend<V, kProf>(p, sm, src, f_level, id, s, lane, warp);
                     }
+                    // everything below the frontier (leaves included)
+                    prof_since<kProf>(sm, kPDescend, t0, lane);
                     // drop frontier entries that no longer reach an undecided lane
                     mm &= __ballot_sync(kFull, ((mm >> lane) & 1u) &&
                                                    reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
                 }
             }
             // objects longer than the learned index's halo live in a side tree
-            if (side_top > 0 && s.U) descend<V>(p, sm, side, side_top, 0, s, lane, warp);
+            if (side_top > 0 && s.U) {
+                const long long t0 = tick<kProf>();
+                descend<V, kProf>(p, sm, side, side_top, 0, s, lane, warp);
+                prof_since<kProf>(sm, kPDescend, t0, lane);
+            }
         }
         uint32_t covered = und0 & ~s.und;
         uint8_t r = sm.res[jl * kTile + i];
@@ -914,16 +963,18 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         }
         sm.res[jl * kTile + i] = r;
     }
+    prof_since<kProf>(sm, kPBlocksWarp, t_active, lane);
 }
 
 // One stage (Algorithm 1 over points / segments / edges, or Algorithm 2 over
 // polygon boxes) for the strip: cull through the R-tree or the learned
 // index, then every block.
-template <class V>
+template <class V, bool kProf>
 __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* obj, const uint32_t* ids,
                       const TreeArg& st, const void* sobj, const uint32_t* sids, const LModel* m, int32_t halo,
                       int32_t X0, int32_t Y0, int strip, int z, int32_t R, bool mask_mode, int32_t bx0, int32_t by0,
                       int32_t bx1, int32_t by1, int tid) {
+    const long long t_cull = tick<kProf>();
     set_levels(sm, 0, t, tid);
     set_levels(sm, 1, st, tid);
     if (tid == 0) sm.next_block = 0;
@@ -932,6 +983,7 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
         cull(p, t, V::kFill, sm, bx0, by0, bx1, by1, tid);
     else
         learned_cull(p, t, *m, halo, sm, bx0, by0, bx1, by1, tid);
+    if (tid == 0) prof_since<kProf>(sm, kPCull, t_cull, 0);
     int4 sb = st.root_box;
     bool side_hit = st.top > 0 && sb.x <= bx1 && sb.z >= bx0 && sb.y <= by1 && sb.w >= by0;
     if (sm.f_count > 0 || side_hit) {
@@ -939,10 +991,15 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
         // frontier (a strip reached only by the side tree), so that the
         // blocks never read the lists of an earlier stage
         const int32_t off = (V::kFill || mask_mode) ? 0 : ((1 << (23 - z)) >> 2);
+        const long long t_bin = tick<kProf>();
         bin_frontier(sm, X0, 23 - z, (V::kFill ? 0 : R) + off, tid);
+        if (tid == 0) prof_since<kProf>(sm, kPBin, t_bin, 0);
+        const long long t_blocks = tick<kProf>();
         Src src{obj, ids, t.n_obj, t.nodes, sm.lvl_base[0], sm.lvl_n[0]};
         Src side{sobj, sids, st.n_obj, st.nodes, sm.lvl_base[1], sm.lvl_n[1]};
-        blocks_pass<V>(p, sm, src, side, side_hit ? st.top : 0, X0, Y0, strip, z, R, mask_mode, tid);
+        blocks_pass<V, kProf>(p, sm, src, side, side_hit ? st.top : 0, X0, Y0, strip, z, R, mask_mode, tid);
+        __syncthreads();
+        if (tid == 0) prof_since<kProf>(sm, kPBlocksCta, t_blocks, 0);
     }
     __syncthreads();
 }
@@ -981,10 +1038,14 @@ __device__ void decode_outline(const Params& p, const uint8_t* out, Smem& sm, in
     }
 }
 
-template <int kKind>
+template <int kKind, bool kProf>
 __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_render(const Params p) {
     __shared__ Smem sm;
     const int tid = threadIdx.x;
+    const long long t_start = tick<kProf>();
+    if constexpr (kProf) {
+        if (tid < kPN) sm.prof[tid] = 0;
+    }
     const int rows = p.rows;
     const uint32_t tile = blockIdx.x / p.strips;
     const int strip = blockIdx.x % p.strips;
@@ -1000,6 +1061,7 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
         if (tid == 0 && strip == 0) atomicOr(p.status, 1u);
     }
     __syncthreads();
+    if (tid == 0) prof_since<kProf>(sm, kPPrologue, t_start, 0);
     const bool mask_mode = p.mode == HV_MODE_MASK;
     if (ok) {
         const int z = q.z;
@@ -1015,22 +1077,23 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
         const bool learned = p.use_learned != 0;
         // Algorithm 1 over points / segments / polygon edges
         if constexpr (kKind == HV_LAYER_POINTS)
-            stage<PointLeaf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
+            stage<PointLeaf, kProf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
                              p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
         else if constexpr (kKind != kPolyFill)
-            stage<SegLeaf<kKind == HV_LAYER_LINES>>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
+            stage<SegLeaf<kKind == HV_LAYER_LINES>, kProf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
                            p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
         // Algorithm 2 over polygon boxes and edges
         if constexpr (kKind == kPolyFill) {
             const int32_t cx0 = X0 + (ps >> 1), cx1 = X0 + (kTile - 1) * ps + (ps >> 1);
             const int32_t cy0 = Y0 + strip * rows * ps + (ps >> 1);
             const int32_t cy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1);
-            stage<FillLeaf>(p, sm, p.mtree, p.mbr_obj, p.mbr_ids, p.mside, p.mside_obj, p.mside_ids,
+            stage<FillLeaf, kProf>(p, sm, p.mtree, p.mbr_obj, p.mbr_ids, p.mside, p.mside_obj, p.mside_ids,
                             learned ? &p.mlm : nullptr, p.mhalo, X0, Y0, strip, z, 0, mask_mode, cx0, cy0, cx1,
                             cy1, tid);
         }
     }
     // ---- encode the strip (Sec. 4.1 Render Tiles) ----
+    const long long t_enc = tick<kProf>();
     uint8_t* out = p.out + (uint64_t)tile * p.tile_bytes;
     if (p.mode == HV_MODE_MASK) {
         // 16 rows x 8 words; word w of row j = pixels 32w .. 32w+31
@@ -1080,6 +1143,20 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
             }
             o4[it * kThreads + tid] = make_uint4(w[0], w[1], w[2], w[3]);
         }
+    }
+    if constexpr (kProf) {
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned long long now = (unsigned long long)clock64();
+            sm.prof[kPEncode] += now - (unsigned long long)t_enc;
+            sm.prof[kPTotal] += now - (unsigned long long)t_start;
+            sm.prof[kPCtas] = 1;
+            // CTA-wide phases hold every warp of the CTA
+            const int cta_phases[6] = {kPTotal, kPPrologue, kPCull, kPBin, kPBlocksCta, kPEncode};
+            for (int k = 0; k < 6; k++) sm.prof[cta_phases[k]] *= kWarps;
+        }
+        __syncthreads();
+        if (tid < kPN && sm.prof[tid]) atomicAdd(p.phases + tid, sm.prof[tid]);
     }
 }
 
@@ -1156,7 +1233,9 @@ int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int
         p.log = (unsigned long long*)log->log;
         p.log_cap = log->cap;
         p.log_n = (unsigned long long*)log->count;
+        p.phases = (unsigned long long*)log->phases;
     }
+    const bool prof = p.phases != nullptr;
     // strip height: 16 rows (16 CTAs per tile) when the batch fills the GPU,
     // 8 or 4 rows for small batches so that a few tiles still spread over
     // many SMs (lower latency)
@@ -1173,13 +1252,26 @@ int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int
         set_error("too many tiles in one call");
         return HV_EINVAL;
     }
-    if (L->kind == HV_LAYER_POINTS)
-        k_render<HV_LAYER_POINTS><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+    if (prof) {
+        // the instrumented instantiations (phase profile); polygon layers
+        // profile their two launches into two halves of the counters
+        if (L->kind == HV_LAYER_POINTS)
+            k_render<HV_LAYER_POINTS, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        else if (L->kind == HV_LAYER_LINES)
+            k_render<HV_LAYER_LINES, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        else {
+            k_render<HV_LAYER_POLYGONS, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+            Params q = p;
+            q.phases = p.phases + kPN;
+            k_render<kPolyFill, true><<<(unsigned)grid, kThreads, 0, stream>>>(q);
+        }
+    } else if (L->kind == HV_LAYER_POINTS)
+        k_render<HV_LAYER_POINTS, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
     else if (L->kind == HV_LAYER_LINES)
-        k_render<HV_LAYER_LINES><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        k_render<HV_LAYER_LINES, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
     else {
-        k_render<HV_LAYER_POLYGONS><<<(unsigned)grid, kThreads, 0, stream>>>(p);
-        k_render<kPolyFill><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        k_render<HV_LAYER_POLYGONS, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        k_render<kPolyFill, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
     }
     HV_CUDA(cudaGetLastError());
     return HV_OK;

@@ -98,6 +98,7 @@ SIGNATURES = {
     "hv_render_tiles_static": [P, P, U32, I32, I32, P, P, U64, P],
     "hv_layer_take_status": [P, P, ctypes.POINTER(U32)],
     "hv_render_tiles_counted": [P, P, U32, I32, I32, P, P, U64, P, U64, P, P],
+    "hv_render_tiles_phases": [P, P, U32, I32, I32, P, P, U64, P, P],
     "hv_render_launches": [P, I32, ctypes.POINTER(U32)],
     "hv_server_start": [P, P, U32, ctypes.POINTER(hv_server_opts), ctypes.POINTER(P)],
     "hv_server_submit": [P, P, U64],
@@ -286,6 +287,19 @@ def hv_render_tiles_counted(layer, reqs, n, mode, index_kind, style, out, out_by
                                          ctypes.byref(style) if style is not None else None, ptr(out),
                                          out_bytes, ptr(log), log_cap, ptr(log_count),
                                          stream_handle(stream)))
+
+
+PHASE_NAMES = ["total", "prologue", "cull", "bin", "blocks_cta", "blocks_warp", "leaf", "descend", "encode",
+               "ctas", "blocks", "leaf_visits", "node_visits", "frontier_tests"]
+HV_PHASE_COUNT = 16
+
+
+def hv_render_tiles_phases(layer, reqs, n, mode, index_kind, style, out, out_bytes, phases, stream=None):
+    """Instrumented render: adds per-phase warp-cycles into `phases` (device,
+    HV_PHASE_COUNT uint64, twice that for polygon layers)."""
+    _check(lib().hv_render_tiles_phases(layer, ptr(reqs), n, mode, index_kind,
+                                        ctypes.byref(style) if style is not None else None, ptr(out),
+                                        out_bytes, ptr(phases), stream_handle(stream)))
 
 
 def hv_render_tiles_static(layer, reqs, n, mode, index_kind, style, out, out_bytes, stream=None):

@@ -400,3 +400,46 @@ def test_host_output_in_chunks(ctx):
         assert np.array_equal(pinned.numpy(), render_dev(L, reqs, hv.HV_MODE_MASK))
     finally:
         hv.hv_layer_free(L)
+
+
+@pytest.mark.parametrize("kind", ["points", "lines", "polygons"])
+def test_phase_profile_launch(ctx, kind):
+    """The instrumented (phase-profile) launch renders the oracle's tiles, and
+    its counters nest: the launch holds the block phase, busy warps are part
+    of it, descents part of those, leaf visits part of the descents."""
+    if kind == "points":
+        pts = gen.gmm_points(80_000, seed=31, k=8)
+        L = hv.hv_layer_load_points(ctx, pts)
+        reqs = gen.density_tiles(pts, 30, 3, 14, [8, 32], seed=32)
+        ref = lambda r, m: oracle.render_points(pts, r, m, STYLE_T)
+    elif kind == "lines":
+        xy, off = gen.walk_lines(4_000, 30_000, seed=33, n_cities=10)
+        L = hv.hv_layer_load_linestrings(ctx, xy, off)
+        reqs = gen.density_tiles(gen.segment_midpoints(xy, off, 2000), 30, 3, 15, [8, 24], seed=34)
+        ref = lambda r, m: oracle.render_lines(xy, off, r, m, STYLE_T)
+    else:
+        xy, ro, po = gen.star_polygons(3_000, seed=35, k=8, rho_median=6e-4)
+        L = hv.hv_layer_load_polygons(ctx, xy, ro, po)
+        reqs = gen.density_tiles(gen.polygon_centres(xy, ro, po), 20, 3, 12, 8, seed=36)
+        ref = lambda r, m: oracle.render_polygons(xy, ro, po, r, m, STYLE_T)
+    hv.hv_layer_build_index(L, hv.HV_INDEX_RTREE | hv.HV_INDEX_LEARNED)
+    try:
+        for index in (hv.HV_INDEX_RTREE, hv.HV_INDEX_LEARNED):
+            n = len(reqs)
+            d_req = torch.from_numpy(hv.make_requests(reqs).view(np.uint8).copy()).cuda()
+            out = torch.full((n, hv.hv_tile_bytes(hv.HV_MODE_RGBA)), 0xAB, dtype=torch.uint8, device="cuda")
+            ph = torch.zeros(2 * hv.HV_PHASE_COUNT, dtype=torch.int64, device="cuda")
+            hv.hv_render_tiles_phases(L, d_req, n, hv.HV_MODE_RGBA, index, style(), out, out.numel(), ph)
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy(), ref(reqs, hv.HV_MODE_RGBA))
+            v = ph.cpu().numpy()
+            for part in range(2 if kind == "polygons" else 1):
+                c = v[16 * part:16 * part + 16]
+                assert c[9] in (n * 16, n * 32, n * 64)         # one CTA per strip of 16, 8 or 4 rows
+                assert c[0] >= c[4] >= c[5] >= c[7] >= c[6] > 0
+                assert c[0] >= c[1] + c[2] + c[3] + c[4] + c[8]
+                assert 0 < c[10] <= n * 2048                    # 8 x 4 blocks of strips with work
+            if kind != "polygons":
+                assert not v[16:].any()
+    finally:
+        hv.hv_layer_free(L)
