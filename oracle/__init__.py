@@ -56,11 +56,17 @@ def bind(path: str):
     lib = ctypes.CDLL(path)
     p = ctypes.c_void_p
     u64 = ctypes.c_uint64
+    i64 = ctypes.c_int64
     lib.oracle_render_points.argtypes = [p, u64, p, p, p, p, u64, ctypes.c_int, p, p]
     lib.oracle_render_lines.argtypes = [p, u64, p, u64, p, p, p, p, u64, ctypes.c_int, p, p]
     lib.oracle_render_polygons.argtypes = [p, u64, p, u64, p, u64, p, p, p, p, u64,
                                            ctypes.c_int, p, p]
-    for f in (lib.oracle_render_points, lib.oracle_render_lines, lib.oracle_render_polygons):
+    lib.oracle_render_points_r.argtypes = [p, u64, p, p, p, p, u64, i64, ctypes.c_int, p, p]
+    lib.oracle_render_lines_r.argtypes = [p, u64, p, u64, p, p, p, p, u64, i64, ctypes.c_int, p, p]
+    lib.oracle_render_polygons_r.argtypes = [p, u64, p, u64, p, u64, p, p, p, p, u64, i64,
+                                             ctypes.c_int, p, p]
+    for f in (lib.oracle_render_points, lib.oracle_render_lines, lib.oracle_render_polygons,
+              lib.oracle_render_points_r, lib.oracle_render_lines_r, lib.oracle_render_polygons_r):
         f.restype = ctypes.c_int
     lib.oracle_tile_bytes.argtypes = [ctypes.c_int]
     lib.oracle_tile_bytes.restype = u64
@@ -103,19 +109,24 @@ def _check(rc):
         raise MemoryError("oracle: allocation failed")
 
 
-def render_points(xy, reqs, mode, style=None, lib=None):
-    """Points ``xy`` (n, 2) int32 -> (n_req, tile_bytes) uint8."""
+def render_points(xy, reqs, mode, style=None, lib=None, R_units=None):
+    """Points ``xy`` (n, 2) int32 -> (n_req, tile_bytes) uint8.  ``R_units``:
+    one radius in grid units for every request (buffer analysis) instead of
+    each request's r16."""
     lib = _load(lib)
     xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
     cols, n = _req_cols(reqs)
     st = _style(style)
     out = np.zeros((n, tile_bytes(mode)), dtype=np.uint8)
-    _check(lib.oracle_render_points(_ptr(xy), xy.shape[0], *[_ptr(c) for c in cols], n,
-                                    mode, _ptr(st), _ptr(out)))
+    args = (_ptr(xy), xy.shape[0], *[_ptr(c) for c in cols], n)
+    if R_units is None:
+        _check(lib.oracle_render_points(*args, mode, _ptr(st), _ptr(out)))
+    else:
+        _check(lib.oracle_render_points_r(*args, int(R_units), mode, _ptr(st), _ptr(out)))
     return out
 
 
-def render_lines(xy, line_off, reqs, mode, style=None, lib=None):
+def render_lines(xy, line_off, reqs, mode, style=None, lib=None, R_units=None):
     """Linestrings: vertices ``xy`` (V, 2), line l = vertices [off[l], off[l+1])."""
     lib = _load(lib)
     xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
@@ -123,12 +134,15 @@ def render_lines(xy, line_off, reqs, mode, style=None, lib=None):
     cols, n = _req_cols(reqs)
     st = _style(style)
     out = np.zeros((n, tile_bytes(mode)), dtype=np.uint8)
-    _check(lib.oracle_render_lines(_ptr(xy), xy.shape[0], _ptr(off), off.shape[0] - 1,
-                                   *[_ptr(c) for c in cols], n, mode, _ptr(st), _ptr(out)))
+    args = (_ptr(xy), xy.shape[0], _ptr(off), off.shape[0] - 1, *[_ptr(c) for c in cols], n)
+    if R_units is None:
+        _check(lib.oracle_render_lines(*args, mode, _ptr(st), _ptr(out)))
+    else:
+        _check(lib.oracle_render_lines_r(*args, int(R_units), mode, _ptr(st), _ptr(out)))
     return out
 
 
-def render_polygons(xy, ring_off, poly_ring_off, reqs, mode, style=None, lib=None):
+def render_polygons(xy, ring_off, poly_ring_off, reqs, mode, style=None, lib=None, R_units=None):
     """Polygons: ring r = vertices [ring_off[r], ring_off[r+1]) (closed implicitly),
     polygon p = rings [poly_ring_off[p], poly_ring_off[p+1])."""
     lib = _load(lib)
@@ -138,9 +152,12 @@ def render_polygons(xy, ring_off, poly_ring_off, reqs, mode, style=None, lib=Non
     cols, n = _req_cols(reqs)
     st = _style(style)
     out = np.zeros((n, tile_bytes(mode)), dtype=np.uint8)
-    _check(lib.oracle_render_polygons(_ptr(xy), xy.shape[0], _ptr(ro), ro.shape[0] - 1,
-                                      _ptr(po), po.shape[0] - 1, *[_ptr(c) for c in cols], n,
-                                      mode, _ptr(st), _ptr(out)))
+    args = (_ptr(xy), xy.shape[0], _ptr(ro), ro.shape[0] - 1, _ptr(po), po.shape[0] - 1,
+            *[_ptr(c) for c in cols], n)
+    if R_units is None:
+        _check(lib.oracle_render_polygons(*args, mode, _ptr(st), _ptr(out)))
+    else:
+        _check(lib.oracle_render_polygons_r(*args, int(R_units), mode, _ptr(st), _ptr(out)))
     return out
 
 

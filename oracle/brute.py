@@ -81,12 +81,15 @@ def edges_of_polygons(polys):
     return segs
 
 
-def pixel_flags(kind, layer, z, tx, ty, r16, i, j):
+def pixel_flags(kind, layer, z, tx, ty, r16, i, j, R=None):
     """Return (centre_hit, [4 sub-sample hits], fill) for one pixel.
 
     kind: 'points' (layer = [(x, y)]), 'lines' (layer = [[(x, y), ...]]),
-    'polygons' (layer = [[ring, ...]] with ring = [(x, y), ...])."""
-    R = r16 << (19 - z)
+    'polygons' (layer = [[ring, ...]] with ring = [(x, y), ...]).  The radius
+    is r16 sixteenths of a pixel, or R grid units when R is given (a buffer
+    distance on the ground)."""
+    if R is None:
+        R = r16 << (19 - z)
     R2 = R * R
     c, subs = samples(z, tx, ty, i, j)
     if kind == "points":
@@ -117,11 +120,11 @@ def encode_pixel(mode, centre, subs, fill, style):
     return (0, 0, 0, 0)
 
 
-def render_window(kind, layer, z, tx, ty, r16, i_range, j_range, mode, style=(0,) * 8):
+def render_window(kind, layer, z, tx, ty, r16, i_range, j_range, mode, style=(0,) * 8, R=None):
     """Dict (i, j) -> encoded pixel for the pixels of a window of one tile."""
     out = {}
     for j in j_range:
         for i in i_range:
-            centre, subs, fill = pixel_flags(kind, layer, z, tx, ty, r16, i, j)
+            centre, subs, fill = pixel_flags(kind, layer, z, tx, ty, r16, i, j, R)
             out[(i, j)] = encode_pixel(mode, centre, subs, fill, style)
     return out

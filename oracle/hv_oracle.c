@@ -19,7 +19,9 @@
  *   samples   : the centre and the four super-samples cx +- ps/4,
  *               cy +- ps/4 (Algorithm 1, the four points P1..P4).
  *   radius    : R = r16 * 2^(19-z) units, r16 = style radius in 1/16 px
- *               (Algorithm 1 step 2, R = N * R_z).
+ *               (Algorithm 1 step 2, R = N * R_z); or, for buffer analysis
+ *               (Sec. 3.2: SIBV extends HiBuffer's buffers, whose distance is
+ *               given on the ground), one R in grid units for every tile.
  *   covered   : C(s, R) = exists an object o with dist(o, s) <= R
  *               (closed comparison, Algorithm 1 "distance <= R").
  *   coverage  : v = number of the four super-samples with C (0..4, the
@@ -132,6 +134,7 @@ static int cmp_ref(const void* a, const void* b) {
 
 typedef struct {
     const uint32_t *z, *x, *y, *r16;
+    int64_t R_fixed;         /* >= 0: the radius of every request (grid units) */
     uint64_t n;
     tile_ref* refs;          /* sorted by key */
     int64_t rmax[32];        /* largest R requested at each zoom, -1 if none */
@@ -140,9 +143,14 @@ typedef struct {
 
 static int64_t radius_units(uint32_t r16, uint32_t z) { return (int64_t)r16 << (19 - z); }
 
+/* The radius of request i. */
+static int64_t request_radius(const req_table* t, uint64_t i) {
+    return t->R_fixed >= 0 ? t->R_fixed : radius_units(t->r16[i], t->z[i]);
+}
+
 static int table_init(req_table* t, const uint32_t* z, const uint32_t* x,
-                      const uint32_t* y, const uint32_t* r16, uint64_t n) {
-    t->z = z; t->x = x; t->y = y; t->r16 = r16; t->n = n;
+                      const uint32_t* y, const uint32_t* r16, uint64_t n, int64_t R_fixed) {
+    t->z = z; t->x = x; t->y = y; t->r16 = r16; t->n = n; t->R_fixed = R_fixed;
     for (int k = 0; k < 32; k++) t->rmax[k] = -1;
     t->refs = (tile_ref*)malloc(sizeof(tile_ref) * (n ? n : 1));
     t->flags = (uint8_t*)calloc(n ? n * TILE_PX * TILE_PX : 1, 1);
@@ -150,7 +158,7 @@ static int table_init(req_table* t, const uint32_t* z, const uint32_t* x,
     for (uint64_t i = 0; i < n; i++) {
         t->refs[i].key = tile_key(z[i], x[i], y[i]);
         t->refs[i].req = (uint32_t)i;
-        int64_t R = radius_units(r16[i], z[i]);
+        int64_t R = request_radius(t, i);
         if (R > t->rmax[z[i]]) t->rmax[z[i]] = R;
     }
     qsort(t->refs, n, sizeof(tile_ref), cmp_ref);
@@ -186,7 +194,7 @@ static void call_request(const req_table* t, uint64_t i, uint32_t z, int64_t tx,
                          const void* obj, splat_fn f) {
     int64_t span = (int64_t)1 << (31 - z);
     uint32_t r = t->refs[i].req;
-    int64_t R = radius_units(t->r16[r], z);
+    int64_t R = request_radius(t, r);
     f(obj, z, -GRID_HALF + tx * span, -GRID_HALF + ty * span, R,
       t->flags + (uint64_t)r * TILE_PX * TILE_PX);
 }
@@ -376,11 +384,12 @@ static void encode(const uint8_t* flags, uint64_t n, int mode, const uint8_t* st
 /* ---- entry points ----------------------------------------------------- */
 
 static int check_requests(const uint32_t* z, const uint32_t* x, const uint32_t* y,
-                          const uint32_t* r16, uint64_t n) {
+                          const uint32_t* r16, uint64_t n, int64_t R_fixed) {
+    if (R_fixed > ((int64_t)1 << 29)) return -2;
     for (uint64_t i = 0; i < n; i++) {
         if (z[i] > 19) return -2;
         if (x[i] >= (1u << z[i]) || y[i] >= (1u << z[i])) return -2;
-        if (r16[i] < 1 || r16[i] > 1024) return -2;
+        if (R_fixed < 0 && (r16[i] < 1 || r16[i] > 1024)) return -2;
     }
     return 0;
 }
@@ -392,12 +401,12 @@ static int check_coords(const int32_t* xy, uint64_t n) {
 }
 
 /* Points: xy = n interleaved (x, y).  Returns 0, -1 (no memory) or -2 (range). */
-int oracle_render_points(const int32_t* xy, uint64_t n, const uint32_t* z, const uint32_t* x,
-                         const uint32_t* y, const uint32_t* r16, uint64_t n_req, int mode,
-                         const uint8_t* style, uint8_t* out) {
-    if (check_requests(z, x, y, r16, n_req) || check_coords(xy, n)) return -2;
+int oracle_render_points_r(const int32_t* xy, uint64_t n, const uint32_t* z, const uint32_t* x,
+                           const uint32_t* y, const uint32_t* r16, uint64_t n_req, int64_t R_fixed, int mode,
+                           const uint8_t* style, uint8_t* out) {
+    if (check_requests(z, x, y, r16, n_req, R_fixed) || check_coords(xy, n)) return -2;
     req_table t;
-    if (table_init(&t, z, x, y, r16, n_req)) { table_free(&t); return -1; }
+    if (table_init(&t, z, x, y, r16, n_req, R_fixed)) { table_free(&t); return -1; }
     for (uint64_t k = 0; k < n; k++) {
         pt_obj o = {xy[2 * k], xy[2 * k + 1]};
         for_each_request(&t, o.x, o.y, o.x, o.y, &o, splat_point);
@@ -409,13 +418,13 @@ int oracle_render_points(const int32_t* xy, uint64_t n, const uint32_t* z, const
 
 /* Linestrings: line l has vertices [line_off[l], line_off[l+1]) and is drawn as
  * its consecutive segments; a line with fewer than two vertices draws nothing. */
-int oracle_render_lines(const int32_t* xy, uint64_t n_vert, const uint64_t* line_off,
-                        uint64_t n_lines, const uint32_t* z, const uint32_t* x,
-                        const uint32_t* y, const uint32_t* r16, uint64_t n_req, int mode,
-                        const uint8_t* style, uint8_t* out) {
-    if (check_requests(z, x, y, r16, n_req) || check_coords(xy, n_vert)) return -2;
+int oracle_render_lines_r(const int32_t* xy, uint64_t n_vert, const uint64_t* line_off,
+                          uint64_t n_lines, const uint32_t* z, const uint32_t* x,
+                          const uint32_t* y, const uint32_t* r16, uint64_t n_req, int64_t R_fixed, int mode,
+                          const uint8_t* style, uint8_t* out) {
+    if (check_requests(z, x, y, r16, n_req, R_fixed) || check_coords(xy, n_vert)) return -2;
     req_table t;
-    if (table_init(&t, z, x, y, r16, n_req)) { table_free(&t); return -1; }
+    if (table_init(&t, z, x, y, r16, n_req, R_fixed)) { table_free(&t); return -1; }
     for (uint64_t l = 0; l < n_lines; l++) {
         for (uint64_t v = line_off[l]; v + 1 < line_off[l + 1]; v++) {
             seg_obj s = {xy[2 * v], xy[2 * v + 1], xy[2 * v + 2], xy[2 * v + 3]};
@@ -433,15 +442,15 @@ int oracle_render_lines(const int32_t* xy, uint64_t n_vert, const uint64_t* line
  * implicitly; polygon p owns rings [poly_ring_off[p], poly_ring_off[p+1])
  * (outer ring and holes alike).  The outline uses the request's radius on
  * every edge; the fill is decided at the pixel centre. */
-int oracle_render_polygons(const int32_t* xy, uint64_t n_vert, const uint64_t* ring_off,
-                           uint64_t n_rings, const uint64_t* poly_ring_off, uint64_t n_polys,
-                           const uint32_t* z, const uint32_t* x, const uint32_t* y,
-                           const uint32_t* r16, uint64_t n_req, int mode, const uint8_t* style,
-                           uint8_t* out) {
+int oracle_render_polygons_r(const int32_t* xy, uint64_t n_vert, const uint64_t* ring_off,
+                             uint64_t n_rings, const uint64_t* poly_ring_off, uint64_t n_polys,
+                             const uint32_t* z, const uint32_t* x, const uint32_t* y,
+                             const uint32_t* r16, uint64_t n_req, int64_t R_fixed, int mode,
+                             const uint8_t* style, uint8_t* out) {
     (void)n_rings;
-    if (check_requests(z, x, y, r16, n_req) || check_coords(xy, n_vert)) return -2;
+    if (check_requests(z, x, y, r16, n_req, R_fixed) || check_coords(xy, n_vert)) return -2;
     req_table t;
-    if (table_init(&t, z, x, y, r16, n_req)) { table_free(&t); return -1; }
+    if (table_init(&t, z, x, y, r16, n_req, R_fixed)) { table_free(&t); return -1; }
     for (uint64_t p = 0; p < n_polys; p++) {
         poly_obj P = {xy, ring_off, poly_ring_off[p], poly_ring_off[p + 1], 0, 0, 0, 0};
         int first = 1;
@@ -465,4 +474,27 @@ int oracle_render_polygons(const int32_t* xy, uint64_t n_vert, const uint64_t* r
     encode(t.flags, n_req, mode, style, out);
     table_free(&t);
     return 0;
+}
+
+/* The same with each request's own radius (R = r16 * 2^(19 - z)). */
+int oracle_render_points(const int32_t* xy, uint64_t n, const uint32_t* z, const uint32_t* x,
+                         const uint32_t* y, const uint32_t* r16, uint64_t n_req, int mode,
+                         const uint8_t* style, uint8_t* out) {
+    return oracle_render_points_r(xy, n, z, x, y, r16, n_req, -1, mode, style, out);
+}
+
+int oracle_render_lines(const int32_t* xy, uint64_t n_vert, const uint64_t* line_off,
+                        uint64_t n_lines, const uint32_t* z, const uint32_t* x,
+                        const uint32_t* y, const uint32_t* r16, uint64_t n_req, int mode,
+                        const uint8_t* style, uint8_t* out) {
+    return oracle_render_lines_r(xy, n_vert, line_off, n_lines, z, x, y, r16, n_req, -1, mode, style, out);
+}
+
+int oracle_render_polygons(const int32_t* xy, uint64_t n_vert, const uint64_t* ring_off,
+                           uint64_t n_rings, const uint64_t* poly_ring_off, uint64_t n_polys,
+                           const uint32_t* z, const uint32_t* x, const uint32_t* y,
+                           const uint32_t* r16, uint64_t n_req, int mode, const uint8_t* style,
+                           uint8_t* out) {
+    return oracle_render_polygons_r(xy, n_vert, ring_off, n_rings, poly_ring_off, n_polys, z, x, y, r16,
+                                    n_req, -1, mode, style, out);
 }

@@ -31,6 +31,8 @@ MUTANTS = {
                     "f(obj, z, -GRID_HALF + ty * span, -GRID_HALF + tx * span, R,"),
     "radius_scale": ("return (int64_t)r16 << (19 - z); }", "return (int64_t)r16 << (18 - z); }"),
     "parity_and_not_xor": ("parity ^= 1;", "parity = 1;"),
+    "buffer_radius_ignored": ("return t->R_fixed >= 0 ? t->R_fixed : radius_units(t->r16[i], t->z[i]);",
+                              "return radius_units(t->r16[i], t->z[i]);"),
 }
 
 
@@ -105,6 +107,10 @@ def _battery(lib):
     got = oracle.render_polygons(xy, ro, po, [[13, 3000, 5000, 6]], COV, lib=lib)[0].reshape(256, 256)
     ref = brute.render_window("polygons", polys, 13, 3000, 5000, 6, range(18, 42), range(18, 42), COV)
     check("brute_polygons", all(got[j, i] == v for (i, j), v in ref.items()))
+    # buffer analysis: a ground radius that r16 cannot express
+    bp = np.array([centre(10, 300, 517, 128, 128)], dtype=np.int32)
+    out = oracle.render_points(bp, [[10, 300, 517, 1]], MASK, lib=lib, R_units=17000)
+    check("buffer_radius", oracle.mask_bits(out[0]).sum() == 13)
     return failed
 
 

@@ -348,6 +348,68 @@ def test_brute_across_zoom_zero_and_nineteen():
         _compare_window("points", layer, out, z, tx, ty, 23, COV, (range(0, 22), range(0, 22)))
 
 
+# ---- buffer analysis: one radius in grid units for every tile ---------------
+
+def _lattice_disc(r_num, r_den):
+    """Pixel centres of a unit lattice within distance r = r_num / r_den of a
+    lattice point: #{(i, j) : i^2 + j^2 <= r^2}, the Gauss circle count."""
+    m = r_num // r_den + 1
+    return sum(1 for i in range(-m, m + 1) for j in range(-m, m + 1) if (i * i + j * j) * r_den * r_den <= r_num * r_num)
+
+
+@pytest.mark.parametrize("z,R", [(10, 10000), (10, 17000), (10, 8191), (10, 8192), (14, 100), (3, 123456789)])
+def test_buffer_radius_gauss_circle(z, R):
+    """A point at a pixel centre with a radius in grid units that r16 cannot
+    express (R / pixel not a multiple of 1/16): the MASK covers the lattice
+    points of the disc of radius R / pixel (R = 8191 and 8192 units at zoom 10
+    straddle one pixel: 1 and 5 pixels)."""
+    tx, ty = (1 << z) // 3, (1 << z) // 5
+    p = np.array([centre(z, tx, ty, 128, 128)], dtype=np.int32)
+    out = oracle.render_points(p, [[z, tx, ty, 1]], MASK, R_units=R)
+    assert mask_count(out) == _lattice_disc(R, 1 << (23 - z))
+    if (z, R) in ((10, 10000), (10, 8192)):
+        assert mask_count(out) == 5
+    if (z, R) == (10, 17000):
+        assert mask_count(out) == 13
+    if (z, R) == (10, 8191):
+        assert mask_count(out) == 1
+
+
+def test_buffer_radius_ignores_r16_and_matches_r16_radius():
+    """The fixed radius replaces every request's own; expressed through r16
+    (R = r16 * 2^(19 - z)) the two paths agree."""
+    rng = np.random.default_rng(31)
+    z, tx, ty = 12, 1000, 2000
+    pts = random_cluster_points(rng, 40, z, tx, ty, 8)
+    a = oracle.render_points(pts, [[z, tx, ty, 24], [z, tx, ty, 1000]], COV, R_units=24 << (19 - z))
+    b = oracle.render_points(pts, [[z, tx, ty, 24]], COV)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[0])
+    with pytest.raises(ValueError):
+        oracle.render_points(pts, [[z, tx, ty, 16]], MASK, R_units=(1 << 29) + 1)
+
+
+@pytest.mark.parametrize("kind", ["points", "lines", "polygons"])
+def test_buffer_radius_brute(kind):
+    """The C oracle with a ground radius against the brute force."""
+    rng = np.random.default_rng(41)
+    z, tx, ty = 13, 3000, 5000
+    R = 3 * ps(z) + 777                           # 3.09 px, not a multiple of 1/16 px
+    if kind == "points":
+        layer = [tuple(map(int, p)) for p in random_cluster_points(rng, 10, z, tx, ty, 5, 30, 30)]
+        out = oracle.render_points(np.array(layer, np.int32), [[z, tx, ty, 1]], COV, R_units=R)[0]
+    elif kind == "lines":
+        layer = random_walk_lines(rng, 3, 4, z, tx, ty, 5, 30, 30, 6)
+        xy, off = lines_to_arrays(layer)
+        out = oracle.render_lines(xy, off, [[z, tx, ty, 1]], COV, R_units=R)[0]
+    else:
+        layer = random_star_polygons(rng, 3, z, tx, ty, 8, 30, 30, 5, holes=True, snap=True)
+        xy, ro, po = polys_to_arrays(layer)
+        out = oracle.render_polygons(xy, ro, po, [[z, tx, ty, 1]], COV, R_units=R)[0]
+    ref = brute.render_window(kind, layer, z, tx, ty, 1, range(16, 44), range(16, 44), COV, R=R)
+    got = out.reshape(256, 256)
+    assert all(got[j, i] == v for (i, j), v in ref.items())
+
+
 def test_rejects_out_of_range():
     pts = np.array([[0, 0]], dtype=np.int32)
     for bad in ([20, 0, 0, 16], [3, 8, 0, 16], [3, 0, 8, 16], [3, 0, 0, 0], [3, 0, 0, 1025]):
