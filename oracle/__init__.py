@@ -65,6 +65,9 @@ def bind(path: str):
     lib.oracle_render_lines_r.argtypes = [p, u64, p, u64, p, p, p, p, u64, i64, ctypes.c_int, p, p]
     lib.oracle_render_polygons_r.argtypes = [p, u64, p, u64, p, u64, p, p, p, p, u64, i64,
                                              ctypes.c_int, p, p]
+    lib.oracle_render_polygons_styled.argtypes = [p, u64, p, u64, p, u64, p, p, p, p, u64, i64, ctypes.c_int,
+                                                  p, ctypes.c_int, p, ctypes.c_uint32, ctypes.c_uint32, p]
+    lib.oracle_render_polygons_styled.restype = ctypes.c_int
     for f in (lib.oracle_render_points, lib.oracle_render_lines, lib.oracle_render_polygons,
               lib.oracle_render_points_r, lib.oracle_render_lines_r, lib.oracle_render_polygons_r):
         f.restype = ctypes.c_int
@@ -142,9 +145,12 @@ def render_lines(xy, line_off, reqs, mode, style=None, lib=None, R_units=None):
     return out
 
 
-def render_polygons(xy, ring_off, poly_ring_off, reqs, mode, style=None, lib=None, R_units=None):
+def render_polygons(xy, ring_off, poly_ring_off, reqs, mode, style=None, lib=None, R_units=None, aa=False,
+                    pattern=None):
     """Polygons: ring r = vertices [ring_off[r], ring_off[r+1]) (closed implicitly),
-    polygon p = rings [poly_ring_off[p], poly_ring_off[p+1])."""
+    polygon p = rings [poly_ring_off[p], poly_ring_off[p+1]).  ``aa``: the
+    fill decided at the four super-samples (COVERAGE byte = v | f << 4);
+    ``pattern``: (h, w, 4) uint8 RGBA texels over the global pixel grid."""
     lib = _load(lib)
     xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
     ro = np.ascontiguousarray(np.asarray(ring_off, dtype=np.uint64))
@@ -154,7 +160,13 @@ def render_polygons(xy, ring_off, poly_ring_off, reqs, mode, style=None, lib=Non
     out = np.zeros((n, tile_bytes(mode)), dtype=np.uint8)
     args = (_ptr(xy), xy.shape[0], _ptr(ro), ro.shape[0] - 1, _ptr(po), po.shape[0] - 1,
             *[_ptr(c) for c in cols], n)
-    if R_units is None:
+    if aa or pattern is not None:
+        pat = None if pattern is None else np.ascontiguousarray(np.asarray(pattern, dtype=np.uint8))
+        ph, pw = (0, 0) if pat is None else pat.shape[:2]
+        _check(lib.oracle_render_polygons_styled(*args, -1 if R_units is None else int(R_units), mode, _ptr(st),
+                                                 int(bool(aa)), None if pat is None else _ptr(pat), pw, ph,
+                                                 _ptr(out)))
+    elif R_units is None:
         _check(lib.oracle_render_polygons(*args, mode, _ptr(st), _ptr(out)))
     else:
         _check(lib.oracle_render_polygons_r(*args, int(R_units), mode, _ptr(st), _ptr(out)))

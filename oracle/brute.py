@@ -104,6 +104,12 @@ def pixel_flags(kind, layer, z, tx, ty, r16, i, j, R=None):
     return hit(c), [hit(s) for s in subs], fill
 
 
+def fill_samples(layer, z, tx, ty, i, j):
+    """The four super-samples of a pixel inside some polygon (anti-aliased fill)."""
+    _, subs = samples(z, tx, ty, i, j)
+    return [any(_inside(rings, s) for rings in layer) for s in subs]
+
+
 def encode_pixel(mode, centre, subs, fill, style):
     """Bytes of one pixel in COVERAGE (1) or RGBA (2) mode; MASK bit for mode 0."""
     v = sum(1 for s in subs if s)

@@ -35,6 +35,15 @@
  *               when (a.y > c.y) != (b.y > c.y) and its crossing lies
  *               strictly right of c.  The half-open straddle rule stands in
  *               for the paper's IsLevel flag and its segment cutting (Sec. 3.1).
+ *   fill styles (Sec. 3.2.2 fill styles, Sec. 4.1 Pattern Library):
+ *               anti-aliased fill decides f at the four super-samples, as
+ *               Algorithm 1 does for outlines (the fill count is the number
+ *               inside, 0..4); without it the fill count is 4 when the centre
+ *               is inside, else 0.  A pattern is a w x h grid of RGBA texels
+ *               (alpha 0 or 255) laid over the global pixel grid: pixel
+ *               (256 tx + i, 256 ty + j) takes texel ((256 ty + j) mod h,
+ *               (256 tx + i) mod w); a transparent texel leaves the pixel
+ *               unfilled, an opaque one gives the fill colour.
  *
  * The algorithm is deliberately data driven (the flow of Fig. 1-1): every
  * object is visited once, the requested tiles it can touch are looked up,
@@ -58,7 +67,11 @@
 #define F_SUB_SW 4u   /* (cx - q, cy + q) */
 #define F_SUB_SE 8u   /* (cx + q, cy + q) */
 #define F_CENTRE 16u
-#define F_FILL 32u
+#define F_FILL 32u    /* the centre is inside */
+#define F_FSUB_NW 64u /* the super-samples are inside (anti-aliased fill) */
+#define F_FSUB_NE 128u
+#define F_FSUB_SW 256u
+#define F_FSUB_SE 512u
 
 #define TILE_PX 256
 #define GRID_HALF ((int64_t)1 << 30)
@@ -138,7 +151,7 @@ typedef struct {
     uint64_t n;
     tile_ref* refs;          /* sorted by key */
     int64_t rmax[32];        /* largest R requested at each zoom, -1 if none */
-    uint8_t* flags;          /* n * 65536 per-pixel flag bytes */
+    uint16_t* flags;         /* n * 65536 per-pixel flags */
 } req_table;
 
 static int64_t radius_units(uint32_t r16, uint32_t z) { return (int64_t)r16 << (19 - z); }
@@ -153,7 +166,7 @@ static int table_init(req_table* t, const uint32_t* z, const uint32_t* x,
     t->z = z; t->x = x; t->y = y; t->r16 = r16; t->n = n; t->R_fixed = R_fixed;
     for (int k = 0; k < 32; k++) t->rmax[k] = -1;
     t->refs = (tile_ref*)malloc(sizeof(tile_ref) * (n ? n : 1));
-    t->flags = (uint8_t*)calloc(n ? n * TILE_PX * TILE_PX : 1, 1);
+    t->flags = (uint16_t*)calloc(n ? n * TILE_PX * TILE_PX : 1, sizeof(uint16_t));
     if (!t->refs || !t->flags) return -1;
     for (uint64_t i = 0; i < n; i++) {
         t->refs[i].key = tile_key(z[i], x[i], y[i]);
@@ -185,7 +198,7 @@ static int64_t tile_of(int64_t v, uint32_t z) {
 
 /* The object-kind specific work done on one requested tile. */
 typedef void (*splat_fn)(const void* obj, uint32_t z, int64_t X0, int64_t Y0,
-                         int64_t R, uint8_t* flags);
+                         int64_t R, uint16_t* flags);
 
 /* Visit every requested tile whose area lies within the largest requested
  * radius of the box [x0, x1] x [y0, y1] and call f on it. */
@@ -241,7 +254,7 @@ static void pixel_window(int64_t v0, int64_t v1, int64_t R, int64_t origin, int6
 typedef struct { int64_t x, y; } pt_obj;
 
 static void splat_point(const void* obj, uint32_t z, int64_t X0, int64_t Y0, int64_t R,
-                        uint8_t* flags) {
+                        uint16_t* flags) {
     const pt_obj* o = (const pt_obj*)obj;
     int64_t ps = (int64_t)1 << (23 - z), q = ps / 4;
     int64_t i0, i1, j0, j1;
@@ -251,7 +264,7 @@ static void splat_point(const void* obj, uint32_t z, int64_t X0, int64_t Y0, int
         int64_t cy = Y0 + j * ps + ps / 2;
         for (int64_t i = i0; i <= i1; i++) {
             int64_t cx = X0 + i * ps + ps / 2;
-            uint8_t f = 0;
+            uint16_t f = 0;
             if (point_within(o->x, o->y, cx - q, cy - q, R)) f |= F_SUB_NW;
             if (point_within(o->x, o->y, cx + q, cy - q, R)) f |= F_SUB_NE;
             if (point_within(o->x, o->y, cx - q, cy + q, R)) f |= F_SUB_SW;
@@ -267,7 +280,7 @@ static void splat_point(const void* obj, uint32_t z, int64_t X0, int64_t Y0, int
 typedef struct { int64_t ax, ay, bx, by; } seg_obj;
 
 static void splat_segment(const void* obj, uint32_t z, int64_t X0, int64_t Y0, int64_t R,
-                          uint8_t* flags) {
+                          uint16_t* flags) {
     const seg_obj* s = (const seg_obj*)obj;
     int64_t ps = (int64_t)1 << (23 - z), q = ps / 4;
     int64_t x0 = s->ax < s->bx ? s->ax : s->bx, x1 = s->ax < s->bx ? s->bx : s->ax;
@@ -279,7 +292,7 @@ static void splat_segment(const void* obj, uint32_t z, int64_t X0, int64_t Y0, i
         int64_t cy = Y0 + j * ps + ps / 2;
         for (int64_t i = i0; i <= i1; i++) {
             int64_t cx = X0 + i * ps + ps / 2;
-            uint8_t f = 0;
+            uint16_t f = 0;
             if (segment_within(s->ax, s->ay, s->bx, s->by, cx - q, cy - q, R)) f |= F_SUB_NW;
             if (segment_within(s->ax, s->ay, s->bx, s->by, cx + q, cy - q, R)) f |= F_SUB_NE;
             if (segment_within(s->ax, s->ay, s->bx, s->by, cx - q, cy + q, R)) f |= F_SUB_SW;
@@ -297,6 +310,7 @@ typedef struct {
     const uint64_t* ring_off; /* ring r = vertices [ring_off[r], ring_off[r+1]) */
     uint64_t r0, r1;          /* this polygon's rings [r0, r1) */
     int64_t x0, y0, x1, y1;   /* its bounding box */
+    int aa;                   /* also decide the four super-samples */
 } poly_obj;
 
 static int polygon_parity(const poly_obj* p, int64_t cx, int64_t cy) {
@@ -314,19 +328,28 @@ static int polygon_parity(const poly_obj* p, int64_t cx, int64_t cy) {
 }
 
 static void splat_fill(const void* obj, uint32_t z, int64_t X0, int64_t Y0, int64_t R,
-                       uint8_t* flags) {
+                       uint16_t* flags) {
     (void)R;
     const poly_obj* p = (const poly_obj*)obj;
-    int64_t ps = (int64_t)1 << (23 - z);
+    int64_t ps = (int64_t)1 << (23 - z), q = ps / 4;
     int64_t i0, i1, j0, j1;
-    /* a centre outside the polygon's box has even parity */
+    /* a sample outside the polygon's box has even parity; the window reaches
+       one pixel past the box, beyond every super-sample inside it */
     pixel_window(p->x0, p->x1, 0, X0, ps, &i0, &i1);
     pixel_window(p->y0, p->y1, 0, Y0, ps, &j0, &j1);
     for (int64_t j = j0; j <= j1; j++) {
         int64_t cy = Y0 + j * ps + ps / 2;
         for (int64_t i = i0; i <= i1; i++) {
             int64_t cx = X0 + i * ps + ps / 2;
-            if (polygon_parity(p, cx, cy)) flags[j * TILE_PX + i] |= F_FILL;
+            uint16_t f = 0;
+            if (polygon_parity(p, cx, cy)) f |= F_FILL;
+            if (p->aa) {
+                if (polygon_parity(p, cx - q, cy - q)) f |= F_FSUB_NW;
+                if (polygon_parity(p, cx + q, cy - q)) f |= F_FSUB_NE;
+                if (polygon_parity(p, cx - q, cy + q)) f |= F_FSUB_SW;
+                if (polygon_parity(p, cx + q, cy + q)) f |= F_FSUB_SE;
+            }
+            flags[j * TILE_PX + i] |= f;
         }
     }
 }
@@ -343,37 +366,67 @@ uint64_t oracle_tile_bytes(int mode) {
     return TILE_PX * TILE_PX * 4;
 }
 
-/* style: line colour r,g,b,(unused) then fill colour r,g,b,(unused). */
-static void encode(const uint8_t* flags, uint64_t n, int mode, const uint8_t* style,
-                   uint8_t* out) {
+/* Fill options of polygon layers: anti-aliased fill and a pattern (NULL
+ * texels: the style's fill colour everywhere). */
+typedef struct {
+    int aa;
+    const uint8_t* pattern;   /* pw * ph RGBA texels, row-major */
+    uint32_t pw, ph;
+} fill_opts;
+
+/* style: line colour r,g,b,(unused) then fill colour r,g,b,(unused).
+ * Per pixel: v = covered outline super-samples, f = fill count (super-samples
+ * inside with anti-aliasing, else 4 when the centre is inside); a pattern
+ * texel that is transparent makes f = 0, an opaque one gives the fill colour.
+ * RGBA composes the outline over the fill: a_o = (255 v + 2) >> 2,
+ * a_f = (255 f + 2) >> 2, A = (255 a_o + a_f (255 - a_o) + 127) / 255 and each
+ * colour channel (line a_o 255 + fill a_f (255 - a_o) + 127 A) / (255 A); with
+ * f = 4 this is (line a_o + fill (255 - a_o) + 127) / 255 with A = 255, with
+ * f = 0 it is the line colour with alpha a_o. */
+static void encode(const uint16_t* flags, const req_table* t, int mode, const uint8_t* style,
+                   const fill_opts* fo, uint8_t* out) {
     uint64_t tb = oracle_tile_bytes(mode);
-    for (uint64_t t = 0; t < n; t++) {
-        const uint8_t* fl = flags + t * TILE_PX * TILE_PX;
-        uint8_t* o = out + t * tb;
+    for (uint64_t k = 0; k < t->n; k++) {
+        const uint16_t* fl = flags + k * TILE_PX * TILE_PX;
+        uint8_t* o = out + k * tb;
         memset(o, 0, tb);
         for (int j = 0; j < TILE_PX; j++) {
             for (int i = 0; i < TILE_PX; i++) {
-                uint32_t f = fl[j * TILE_PX + i];
-                uint32_t v = popcount4(f);
-                uint32_t filled = (f & F_FILL) ? 1u : 0u;
+                uint32_t g = fl[j * TILE_PX + i];
+                uint32_t v = popcount4(g);
+                uint32_t centre_fill = (g & F_FILL) ? 1u : 0u;
+                uint32_t f = (fo && fo->aa) ? popcount4(g >> 6) : 4u * centre_fill;
+                const uint8_t* fill = style + 4;
+                if (fo && fo->pattern) {
+                    uint64_t gx = (uint64_t)t->x[k] * TILE_PX + (uint64_t)i;
+                    uint64_t gy = (uint64_t)t->y[k] * TILE_PX + (uint64_t)j;
+                    const uint8_t* tx = fo->pattern + 4 * ((gy % fo->ph) * fo->pw + gx % fo->pw);
+                    if (tx[3] == 0) { f = 0; centre_fill = 0; }
+                    fill = tx;
+                }
                 if (mode == OR_MODE_MASK) {
-                    if ((f & F_CENTRE) || filled) {
+                    if ((g & F_CENTRE) || centre_fill) {
                         /* bit b of little-endian word w of row j is pixel 32w+b */
                         int w = i / 32, b = i % 32;
                         o[(j * 8 + w) * 4 + b / 8] |= (uint8_t)(1u << (b % 8));
                     }
                 } else if (mode == OR_MODE_COVERAGE) {
-                    o[j * TILE_PX + i] = (uint8_t)(v | (filled << 3));
+                    if (fo && fo->aa)
+                        o[j * TILE_PX + i] = (uint8_t)(v | (f << 4));
+                    else
+                        o[j * TILE_PX + i] = (uint8_t)(v | ((f ? 1u : 0u) << 3));
                 } else {
                     uint8_t* px = o + 4 * (j * TILE_PX + i);
-                    uint32_t alpha = (255u * v + 2u) >> 2;
-                    if (filled) {
+                    uint32_t ao = (255u * v + 2u) >> 2, af = (255u * f + 2u) >> 2;
+                    if (af) {
+                        uint32_t A = (255u * ao + af * (255u - ao) + 127u) / 255u;
                         for (int c = 0; c < 3; c++)
-                            px[c] = (uint8_t)((style[c] * alpha + style[4 + c] * (255u - alpha) + 127u) / 255u);
-                        px[3] = 255;
+                            px[c] = (uint8_t)((style[c] * ao * 255u + fill[c] * af * (255u - ao) + 127u * A) /
+                                              (255u * A));
+                        px[3] = (uint8_t)A;
                     } else if (v) {
                         px[0] = style[0]; px[1] = style[1]; px[2] = style[2];
-                        px[3] = (uint8_t)alpha;
+                        px[3] = (uint8_t)ao;
                     }
                 }
             }
@@ -411,7 +464,7 @@ int oracle_render_points_r(const int32_t* xy, uint64_t n, const uint32_t* z, con
         pt_obj o = {xy[2 * k], xy[2 * k + 1]};
         for_each_request(&t, o.x, o.y, o.x, o.y, &o, splat_point);
     }
-    encode(t.flags, n_req, mode, style, out);
+    encode(t.flags, &t, mode, style, NULL, out);
     table_free(&t);
     return 0;
 }
@@ -433,7 +486,7 @@ int oracle_render_lines_r(const int32_t* xy, uint64_t n_vert, const uint64_t* li
             for_each_request(&t, x0, y0, x1, y1, &s, splat_segment);
         }
     }
-    encode(t.flags, n_req, mode, style, out);
+    encode(t.flags, &t, mode, style, NULL, out);
     table_free(&t);
     return 0;
 }
@@ -442,17 +495,24 @@ int oracle_render_lines_r(const int32_t* xy, uint64_t n_vert, const uint64_t* li
  * implicitly; polygon p owns rings [poly_ring_off[p], poly_ring_off[p+1])
  * (outer ring and holes alike).  The outline uses the request's radius on
  * every edge; the fill is decided at the pixel centre. */
-int oracle_render_polygons_r(const int32_t* xy, uint64_t n_vert, const uint64_t* ring_off,
-                             uint64_t n_rings, const uint64_t* poly_ring_off, uint64_t n_polys,
-                             const uint32_t* z, const uint32_t* x, const uint32_t* y,
-                             const uint32_t* r16, uint64_t n_req, int64_t R_fixed, int mode,
-                             const uint8_t* style, uint8_t* out) {
+int oracle_render_polygons_styled(const int32_t* xy, uint64_t n_vert, const uint64_t* ring_off,
+                                  uint64_t n_rings, const uint64_t* poly_ring_off, uint64_t n_polys,
+                                  const uint32_t* z, const uint32_t* x, const uint32_t* y,
+                                  const uint32_t* r16, uint64_t n_req, int64_t R_fixed, int mode,
+                                  const uint8_t* style, int aa, const uint8_t* pattern, uint32_t pw,
+                                  uint32_t ph, uint8_t* out) {
     (void)n_rings;
     if (check_requests(z, x, y, r16, n_req, R_fixed) || check_coords(xy, n_vert)) return -2;
+    if (pattern) {
+        if (pw < 1 || ph < 1 || pw > 16 || ph > 16) return -2;
+        for (uint32_t k = 0; k < pw * ph; k++)
+            if (pattern[4 * k + 3] != 0 && pattern[4 * k + 3] != 255) return -2;
+    }
+    fill_opts fo = {aa, pattern, pw, ph};
     req_table t;
     if (table_init(&t, z, x, y, r16, n_req, R_fixed)) { table_free(&t); return -1; }
     for (uint64_t p = 0; p < n_polys; p++) {
-        poly_obj P = {xy, ring_off, poly_ring_off[p], poly_ring_off[p + 1], 0, 0, 0, 0};
+        poly_obj P = {xy, ring_off, poly_ring_off[p], poly_ring_off[p + 1], 0, 0, 0, 0, aa};
         int first = 1;
         for (uint64_t r = P.r0; r < P.r1; r++) {
             uint64_t v0 = ring_off[r], v1 = ring_off[r + 1];
@@ -471,9 +531,18 @@ int oracle_render_polygons_r(const int32_t* xy, uint64_t n_vert, const uint64_t*
         }
         if (!first) for_each_request(&t, P.x0, P.y0, P.x1, P.y1, &P, splat_fill);
     }
-    encode(t.flags, n_req, mode, style, out);
+    encode(t.flags, &t, mode, style, &fo, out);
     table_free(&t);
     return 0;
+}
+
+int oracle_render_polygons_r(const int32_t* xy, uint64_t n_vert, const uint64_t* ring_off,
+                             uint64_t n_rings, const uint64_t* poly_ring_off, uint64_t n_polys,
+                             const uint32_t* z, const uint32_t* x, const uint32_t* y,
+                             const uint32_t* r16, uint64_t n_req, int64_t R_fixed, int mode,
+                             const uint8_t* style, uint8_t* out) {
+    return oracle_render_polygons_styled(xy, n_vert, ring_off, n_rings, poly_ring_off, n_polys, z, x, y, r16,
+                                         n_req, R_fixed, mode, style, 0, NULL, 0, 0, out);
 }
 
 /* The same with each request's own radius (R = r16 * 2^(19 - z)). */

@@ -13,7 +13,7 @@ from geom import (at, centre, coverage_fill, golden, lines_to_arrays, polys_to_a
 SRC = os.path.join(os.path.dirname(oracle.__file__), "hv_oracle.c")
 GOLD = golden("closed_forms.json")
 Z, TX, TY = 10, 300, 517
-MASK, COV = oracle.MODE_MASK, oracle.MODE_COVERAGE
+MASK, COV, RGBA = oracle.MODE_MASK, oracle.MODE_COVERAGE, oracle.MODE_RGBA
 
 MUTANTS = {
     "open_disc": ("return dx * dx + dy * dy <= R * R;", "return dx * dx + dy * dy < R * R;"),
@@ -31,6 +31,9 @@ MUTANTS = {
                     "f(obj, z, -GRID_HALF + ty * span, -GRID_HALF + tx * span, R,"),
     "radius_scale": ("return (int64_t)r16 << (19 - z); }", "return (int64_t)r16 << (18 - z); }"),
     "parity_and_not_xor": ("parity ^= 1;", "parity = 1;"),
+    "aa_count_shifted": ("uint32_t f = (fo && fo->aa) ? popcount4(g >> 6) : 4u * centre_fill;",
+                         "uint32_t f = (fo && fo->aa) ? popcount4(g >> 5) : 4u * centre_fill;"),
+    "pattern_transposed": ("4 * ((gy % fo->ph) * fo->pw + gx % fo->pw)", "4 * ((gx % fo->ph) * fo->pw + gy % fo->pw)"),
     "buffer_radius_ignored": ("return t->R_fixed >= 0 ? t->R_fixed : radius_units(t->r16[i], t->z[i]);",
                               "return radius_units(t->r16[i], t->z[i]);"),
 }
@@ -111,6 +114,26 @@ def _battery(lib):
     bp = np.array([centre(10, 300, 517, 128, 128)], dtype=np.int32)
     out = oracle.render_points(bp, [[10, 300, 517, 1]], MASK, lib=lib, R_units=17000)
     check("buffer_radius", oracle.mask_bits(out[0]).sum() == 13)
+    # fill styles: the anti-aliased square and a pattern that is not symmetric
+    k = 5
+    xy, ro, po = polys_to_arrays([[ring_px(Z, TX, TY, 60, 70, [(0, 0), (k, 0), (k, k), (0, k)])]])
+    f = oracle.render_polygons(xy, ro, po, [[Z, TX, TY, 1]], COV, lib=lib, aa=True)[0].reshape(256, 256) >> 4
+    check("aa_square", int(f.sum()) == 4 * k * k and (f == 1).sum() == 4)
+    polys = random_star_polygons(np.random.default_rng(44), 3, 13, 3000, 5000, 8, 30, 30, 5, holes=True, snap=True)
+    xy, ro, po = polys_to_arrays(polys)
+    f = oracle.render_polygons(xy, ro, po, [[13, 3000, 5000, 4]], COV, lib=lib, aa=True)[0].reshape(256, 256) >> 4
+    check("aa_brute", all(f[j, i] == sum(brute.fill_samples(polys, 13, 3000, 5000, i, j))
+                          for j in range(18, 42) for i in range(18, 42)))
+    pat = np.zeros((2, 4, 4), dtype=np.uint8)
+    pat[0, 1] = (1, 2, 3, 255)
+    pat[1, 3] = (4, 5, 6, 255)
+    half = (1 << (22 - Z))
+    xy, ro, po = polys_to_arrays([[[(x - half, y - half) for (x, y) in
+                                    ring_px(Z, TX, TY, 100, 100, [(0, 0), (12, 0), (12, 12), (0, 12)])]]])
+    px = oracle.render_polygons(xy, ro, po, [[Z, TX, TY, 1]], RGBA, lib=lib, pattern=pat)[0].reshape(256, 256, 4)
+    ok = all((px[j, i, 3] == 255) == bool(pat[(256 * TY + j) % 2, (256 * TX + i) % 4, 3])
+             for j in range(100, 112) for i in range(100, 112))
+    check("pattern", ok)
     return failed
 
 

@@ -410,6 +410,134 @@ def test_buffer_radius_brute(kind):
     assert all(got[j, i] == v for (i, j), v in ref.items())
 
 
+# ---- fill styles: anti-aliased fill and pattern fill (Sec. 3.2.2, Sec. 4.1) --
+
+def _centre_square(k, i0=60, j0=70, z=Z, tx=TX, ty=TY):
+    return polys_to_arrays([[ring_px(z, tx, ty, i0, j0, [(0, 0), (k, 0), (k, k), (0, k)])]])
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 9])
+def test_aa_fill_square_on_pixel_centres(k):
+    """A k x k px square with its vertices on pixel centres, fill decided at
+    the super-samples (+-1/4 px) with the half-open rule: the (k-1)^2 pixels
+    strictly inside hold all four samples, the 4(k-1) edge pixels two, the
+    four corner pixels one -- 4 k^2 samples, the square's area in quarter
+    pixels."""
+    xy, ro, po = _centre_square(k)
+    f = oracle.render_polygons(xy, ro, po, req(r16=1), COV, aa=True)[0].reshape(256, 256) >> 4
+    assert int(f.sum()) == 4 * k * k
+    assert (f == 4).sum() == (k - 1) ** 2 and (f == 2).sum() == 4 * (k - 1) and (f == 1).sum() == 4
+    assert f[70 + 1:70 + k, 60 + 1:60 + k].min(initial=4) == 4 and f[70, 60] == 1 and f[70 + k, 60 + k] == 1
+
+
+def test_aa_fill_square_on_pixel_corners_is_exact():
+    """Vertices on pixel corners: every pixel is wholly in or out, so the
+    anti-aliased fill counts 4 or 0 and agrees with the centre fill."""
+    k = 7
+    xy, ro, po = polys_to_arrays([[[(x - ps(Z) // 2, y - ps(Z) // 2) for (x, y) in
+                                    ring_px(Z, TX, TY, 60, 70, [(0, 0), (k, 0), (k, k), (0, k)])]]])
+    cov = oracle.render_polygons(xy, ro, po, req(r16=1), COV, aa=True)[0].reshape(256, 256)
+    plain = oracle.render_polygons(xy, ro, po, req(r16=1), COV)[0].reshape(256, 256)
+    f = cov >> 4
+    assert set(np.unique(f)) == {0, 4} and (f == 4).sum() == k * k
+    assert np.array_equal(f == 4, (plain & 8) != 0)
+
+
+def test_aa_fill_rgba_by_hand():
+    """A square on pixel centres with a hairline outline (r16 = 1: no
+    super-sample within reach of an edge, v = 0): interior pixels take the
+    fill colour opaque, edge pixels (f = 2) the fill colour at alpha
+    (255*2 + 2) >> 2 = 128, corners (f = 1) at alpha 64 -- worked out from
+    A = (a_f * 255 + 127) / 255 = a_f and rgb = (fill * a_f * 255 + 127 a_f) /
+    (255 a_f) = fill."""
+    k = 4
+    xy, ro, po = _centre_square(k)
+    px = oracle.render_polygons(xy, ro, po, req(r16=1), RGBA, STYLE, aa=True)[0].reshape(256, 256, 4)
+    fill = STYLE[4:7]
+    assert tuple(px[72, 62]) == fill + (255,)
+    assert tuple(px[70, 62]) == fill + (128,) and tuple(px[72, 60]) == fill + (128,)
+    assert tuple(px[70, 60]) == fill + (64,) and tuple(px[70 + k, 60 + k]) == fill + (64,)
+    assert tuple(px[69, 62]) == (0, 0, 0, 0)
+
+
+def test_aa_rgba_compose_values_by_hand():
+    """Outline over an anti-aliased fill, values worked out by hand for the
+    line colour (200, 30, 60) over the fill colour (20, 140, 250):
+    v = 2, f = 2: a_o = a_f = 128, A = (255*128 + 128*127 + 127) / 255 = 192,
+      r = (200*128*255 + 20*128*127 + 127*192) / (255*192) = 140, g = 66, b = 123;
+    v = 1, f = 3: a_o = 64, a_f = 191, A = 207, rgb = (76, 106, 191).
+    The pixels are found by their COVERAGE bytes (v | f << 4) in a layer of
+    random polygons with wide outlines."""
+    rng = np.random.default_rng(3)
+    z, tx, ty = 13, 3000, 5000
+    polys = random_star_polygons(rng, 30, z, tx, ty, 20, 128, 128, 60)
+    xy, ro, po = polys_to_arrays(polys)
+    want = {(2, 2): (140, 66, 123, 192), (1, 3): (76, 106, 191, 207)}
+    found = set()
+    for r16 in (2, 4, 6):
+        cov = oracle.render_polygons(xy, ro, po, [[z, tx, ty, r16]], COV, aa=True)[0].reshape(256, 256)
+        px = oracle.render_polygons(xy, ro, po, [[z, tx, ty, r16]], RGBA, STYLE, aa=True)[0].reshape(256, 256, 4)
+        for (v, f), rgba in want.items():
+            jj, ii = np.nonzero(cov == (v | (f << 4)))
+            for j, i in zip(jj[:20], ii[:20]):
+                assert tuple(int(c) for c in px[j, i]) == rgba, (v, f, i, j)
+                found.add((v, f))
+    assert found == set(want)
+
+
+def test_pattern_fill_checkerboard():
+    """A 2 x 2 checkerboard pattern (opaque / transparent texels) over a
+    k x k square with vertices on pixel corners: the filled pixels are those
+    whose global column + row is even (256 is even, so the tile's pixel
+    i + j decides), k^2 / 2 of them, each with its texel's colour."""
+    k = 8
+    red, blue = (250, 10, 10, 255), (10, 10, 250, 255)
+    pat = np.array([[red, (0, 0, 0, 0)], [(0, 0, 0, 0), blue]], dtype=np.uint8)   # [row][column]
+    xy, ro, po = polys_to_arrays([[[(x - ps(Z) // 2, y - ps(Z) // 2) for (x, y) in
+                                    ring_px(Z, TX, TY, 60, 70, [(0, 0), (k, 0), (k, k), (0, k)])]]])
+    m = oracle.mask_bits(oracle.render_polygons(xy, ro, po, req(r16=1), MASK, pattern=pat)[0])
+    assert m.sum() == k * k // 2
+    jj, ii = np.nonzero(m)
+    assert ((ii + jj) % 2 == 0).all()
+    px = oracle.render_polygons(xy, ro, po, req(r16=1), RGBA, STYLE, pattern=pat)[0].reshape(256, 256, 4)
+    assert tuple(px[70, 60]) == red[:3] + (255,) and tuple(px[71, 61]) == blue[:3] + (255,)
+    assert tuple(px[70, 61]) == (0, 0, 0, 0)
+
+
+def test_pattern_is_anchored_to_the_global_pixel_grid():
+    """A 4-wide, 2-high pattern: texel (row gy mod 2, column gx mod 4) of the
+    global pixel (256 tx + i, 256 ty + j), so neighbouring tiles continue it."""
+    k = 12
+    pat = np.zeros((2, 4, 4), dtype=np.uint8)
+    pat[0, 1] = (1, 2, 3, 255)
+    pat[1, 3] = (4, 5, 6, 255)
+    for tx, ty in ((TX, TY), (TX + 1, TY), (TX, TY + 3)):
+        xy, ro, po = polys_to_arrays([[[(x - ps(Z) // 2, y - ps(Z) // 2) for (x, y) in
+                                        ring_px(Z, tx, ty, 100, 100, [(0, 0), (k, 0), (k, k), (0, k)])]]])
+        px = oracle.render_polygons(xy, ro, po, [[Z, tx, ty, 1]], RGBA, STYLE, pattern=pat)[0].reshape(256, 256, 4)
+        for j in range(100, 100 + k):
+            for i in range(100, 100 + k):
+                gx, gy = 256 * tx + i, 256 * ty + j
+                t = pat[gy % 2, gx % 4]
+                want = tuple(int(c) for c in t[:3]) + (255,) if t[3] else (0, 0, 0, 0)
+                assert tuple(int(c) for c in px[j, i]) == want
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_aa_fill_brute(seed):
+    """The anti-aliased fill counts against the brute force's super-sample
+    ray casting, holes and lattice vertices included."""
+    rng = np.random.default_rng(seed + 40)
+    z, tx, ty = 13, 3000, 5000
+    polys = random_star_polygons(rng, 4, z, tx, ty, 8, 30, 30, 5, holes=True, snap=True)
+    xy, ro, po = polys_to_arrays(polys)
+    f = oracle.render_polygons(xy, ro, po, [[z, tx, ty, 4]], COV, aa=True)[0].reshape(256, 256) >> 4
+    layer = [[[tuple(map(int, v)) for v in ring] for ring in rings] for rings in polys]
+    for j in range(16, 44):
+        for i in range(16, 44):
+            assert f[j, i] == sum(brute.fill_samples(layer, z, tx, ty, i, j)), (i, j)
+
+
 def test_rejects_out_of_range():
     pts = np.array([[0, 0]], dtype=np.int32)
     for bad in ([20, 0, 0, 16], [3, 8, 0, 16], [3, 0, 8, 16], [3, 0, 0, 0], [3, 0, 0, 1025]):
