@@ -8,8 +8,9 @@ hv_render_tiles (device-resident requests and output).  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
-Multi-GPU (torchrun): every rank holds a replica of the layer and renders its
-own batch of tiles (weak scaling, no collective on the data path).
+Multi-GPU (torchrun): every rank holds a replica of the layer and renders the
+tiles the tile router (hv_route_tiles) sends it out of a batch of N x 10,000
+(weak scaling, no collective on the data path).
 """
 import argparse
 import json
@@ -71,6 +72,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--index", default="rtree", choices=["rtree", "learned"],
                     help="index timed for the headline value (both are reported)")
+    ap.add_argument("--no-host-placement", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="only the clustered-points line, without the blocks of the other workloads")
     ap.add_argument("--profile-steps", action="store_true",
@@ -247,7 +249,12 @@ class Layer:
             ro = np.asarray(self.ro, dtype=np.int64)
             po = np.asarray(self.po, dtype=np.int64)
             self.poly_edges = ro[po[1:]] - ro[po[:-1]]
-        self.reqs = gen.shard(all_reqs, rank, world)
+        if world > 1:
+            # replicas: the tile router sends each tile to one rank
+            from paper_2005_12489_gb300 import hv
+            self.reqs = all_reqs[hv.hv_route_tiles(all_reqs, world) == rank]
+        else:
+            self.reqs = all_reqs
         self.n_objects = n
 
     def load(self, hv, ctx):
@@ -424,7 +431,7 @@ def phase_profile(hv, torch, layer, d_req, n, mode, index, style, d_out, kind):
     torch.cuda.synchronize()
     v = ph.cpu().numpy().astype(np.float64)
     parts = {}
-    for k, name in enumerate(["outline", "fill"] if kind == "polygons" else ["render"]):
+    for k, name in enumerate(["fill", "outline"] if kind == "polygons" else ["render"]):
         c = v[hv.HV_PHASE_COUNT * k:hv.HV_PHASE_COUNT * (k + 1)]
         tot = max(c[0], 1.0)
         busy, leaf, desc = c[5], c[6], c[7]
@@ -530,11 +537,15 @@ def measure_batch(args, cfg, steps, warmup, dist=None, headline=False, r16_sweep
     clk = clocks.stop()
     step_ms = [x.elapsed_time(y) for x, y in ev]
     ms = sum(step_ms) / len(step_ms)
+    total = n
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * n / (ms / 1000.0)
+        tn = torch.tensor([n], dtype=torch.int64, device="cuda")
+        dist.all_reduce(tn, op=dist.ReduceOp.SUM)
+        total = int(tn.item())
+    value = total / (ms / 1000.0)
     out = None
     if rank == 0 and not args.profile_steps:
         lat = {"rtree": _latency(hv, torch, layer, d_req, n, mode, hv.HV_INDEX_RTREE, style, stream)}
@@ -568,6 +579,25 @@ def measure_batch(args, cfg, steps, warmup, dist=None, headline=False, r16_sweep
         if want_learned:
             phases["learned"] = phase_profile(hv, torch, layer, d_req, n, mode, hv.HV_INDEX_LEARNED, style, d_out,
                                               lay.kind)
+        placed = None
+        if headline and not args.no_host_placement:
+            # the same layer with its index records in host memory, read over
+            # the CPU-GPU link (NVLink-C2C): what a layer larger than the
+            # device's memory would run at
+            hl = lay.load(hv, ctx)
+            opts = hv.hv_build_opts()
+            opts.object_placement = hv.HV_PLACE_HOST
+            hv.hv_layer_build_index(hl, hv.HV_INDEX_RTREE, opts)
+            hinfo = hv.hv_layer_info_get(hl)
+
+            def hstep():
+                hv.hv_render_tiles(hl, d_req, n, mode, hv.HV_INDEX_RTREE, style, d_out, d_out.numel(), stream)
+            hms = statistics.mean(_timed(hstep, flush, stream, k_side))
+            placed = {"value": n / (hms / 1000.0), "unit": "tiles/s", "ms_per_step": hms,
+                      "over_device_resident": ms / hms, "host_bytes": hinfo.host_bytes,
+                      "device_bytes": hinfo.device_bytes,
+                      "placement": "index records in pinned host memory (mapped), nodes and keys in HBM"}
+            hv.hv_layer_free(hl)
         full_size = (args.points is None and args.r16 is None and n == w["tiles_per_step"]) or not headline
         alg = algorithmic_bytes_per_tile(hv, layer, reqs, torch, args.count_sample_tiles, lay)
         roof = _roofline(alg, n, ms, cfg, full_size)
@@ -583,10 +613,23 @@ def measure_batch(args, cfg, steps, warmup, dist=None, headline=False, r16_sweep
             for _ in range(k_e2e):
                 hv.hv_render_tiles(layer, h_req, n, mode, main_index, style, h_out, h_out.numel(), stream)
             dt = (time.perf_counter() - t1) / k_e2e
+            # the copy bound: a plain pinned device -> host copy of 1 GiB
+            cb = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+            hb = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+            hb.copy_(cb)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            for _ in range(3):
+                hb.copy_(cb)
+            torch.cuda.synchronize()
+            d2h = 3 * (1 << 30) / (time.perf_counter() - t2) / 1e9
+            del cb, hb
             e2e = {"value": n / dt, "unit": "tiles/s", "h2d_bytes_per_step": int(h_req.nbytes),
                    "d2h_bytes_per_step": int(n * tb), "ms_per_step": 1000 * dt,
-                   "over_device": (n / dt) / (n / (ms / 1000.0)),
-                   "path": "hv_render_tiles with host requests and pinned host output"}
+                   "over_device": (n / dt) / (n / (ms / 1000.0)), "d2h_copy_GBps": d2h,
+                   "copy_bound_ms": n * tb / d2h / 1e6,
+                   "path": "hv_render_tiles with host requests and pinned host output (the kernels write the "
+                           "tiles into it over the CPU-GPU link)"}
         n_cpu = args.cpu_sample_tiles or {2: 48, 3: 8, 4: 4}[cfg]
         cpu = None if args.no_cpu_baseline else cpu_baseline(lay, n_cpu)
         cpu_mt = None if args.no_cpu_baseline else cpu_rtree_baseline(lay, {2: 96, 3: 48, 4: 16}[cfg])
@@ -604,6 +647,7 @@ def measure_batch(args, cfg, steps, warmup, dist=None, headline=False, r16_sweep
                "e2e": e2e, "gpu_launches": launches_per_step * steps, "clocks": clk,
                "index_timed": "rtree" if main_index == hv.HV_INDEX_RTREE else "learned",
                "learned": learned, "latency": lat, "r16_sweep": sweep, "phases": phases,
+               "host_resident": placed,
                "wall_s_timed_region": wall, "step_ms": step_ms,
                "index_build_ms": info.build_ms, "tree_levels": info.tree_levels,
                "index_records": info.index_records, "piece_extent": info.piece_extent}
@@ -658,11 +702,24 @@ def _serve_rate(hv, ctx, layers, reqs, arrival, index, style, max_batch=64):
                                index_kind=index, use_graphs=1, style=style)
     srv = hv.hv_server_start(ctx, layers, opts)
     try:
-        lat, wall = hv.hv_server_replay(srv, reqs, arrival)
+        lat, parts, wall = hv.hv_server_replay_detail(srv, reqs, arrival)
         st = hv.hv_server_stats(srv)
     finally:
         hv.hv_server_stop(srv)
-    return lat, wall, st
+    return lat, parts, wall, st
+
+
+def _latency_parts(lat, parts):
+    """p50 / p99 of each part of the served latency, and the mean parts of
+    the requests at or above the p99 latency (what the tail is made of)."""
+    names = ("pre_submit", "task_pool", "service", "handout")
+    tail = lat >= np.percentile(lat, 99)
+    out = {}
+    for k, nm in enumerate(names):
+        out[nm] = {"p50_ms": float(np.percentile(parts[:, k], 50)) / 1000,
+                   "p99_ms": float(np.percentile(parts[:, k], 99)) / 1000,
+                   "tail_mean_ms": float(parts[tail, k].mean()) / 1000}
+    return out
 
 
 def serving_block(args):
@@ -700,11 +757,12 @@ def serving_block(args):
         reqs["mode"] = hv.HV_MODE_RGBA
         arrival = np.zeros(len(reqs)) if rate == "inf" else gen.poisson_arrivals(len(reqs), float(rate), seed=600 + ri)
         for index in (hv.HV_INDEX_LEARNED, hv.HV_INDEX_RTREE):
-            lat, wall, st = _serve_rate(hv, ctx, layers, reqs, arrival, index, style)
+            lat, parts, wall, st = _serve_rate(hv, ctx, layers, reqs, arrival, index, style)
             results.append({"rate": rate, "index": "learned" if index == hv.HV_INDEX_LEARNED else "rtree",
                             "requests": len(reqs), "tiles_per_s": len(reqs) / (wall / 1e6),
                             "p50_ms": float(np.percentile(lat, 50)) / 1000,
                             "p99_ms": float(np.percentile(lat, 99)) / 1000,
+                            "parts": _latency_parts(lat, parts),
                             "mean_batch": st["tiles"] / max(1, st["batches"]), "slots": st["slots"],
                             "graph_launches": st["graph_launches"]})
             print(json.dumps(results[-1]), file=sys.stderr, flush=True)
@@ -729,6 +787,9 @@ def serving_block(args):
         class _L:
             kind = name
             obj_bytes = 8 if li == 0 else 32
+        # one tile at a time (device time of a served request's kernels)
+        row["batch1"] = _latency(hv, torch, layers[li], d_req, len(sel), hv.HV_MODE_RGBA, hv.HV_INDEX_LEARNED,
+                                 style, stream, n_tiles=500)
         alg = algorithmic_bytes_per_tile(hv, layers[li], sel, torch, min(200, len(sel)), _L)
         row["alg_bytes_per_tile"] = alg and alg["per_tile"]
         row["hbm_GBps"] = alg and alg["per_tile"] * row["rtree_tiles_per_s"] / 1e9

@@ -104,6 +104,28 @@ typedef struct hv_style {
     uint8_t fill_rgba[4];  /* polygon interiors */
 } hv_style;
 
+/* Fill style of polygon layers (Sec. 3.2.2 fill styles; Sec. 4.1 Pattern
+ * Library).  HV_FILL_AA decides the fill at the four super-samples, as
+ * Algorithm 1 does for outlines: f = number of them inside a polygon (0..4);
+ * COVERAGE then holds v | f << 4 (bits 4-6; bit 3 unused) and RGBA composes
+ * the outline over the partly covered fill (below); MASK keeps the centre
+ * rule.  A pattern of pattern_w x pattern_h texels (1..16 each, RGBA, row
+ * major, alpha 0 or 255) is laid over the global pixel grid: pixel
+ * (256 x + i, 256 y + j) of tile (z, x, y) takes texel
+ * ((256 y + j) mod pattern_h, (256 x + i) mod pattern_w); a transparent
+ * texel leaves the pixel unfilled, an opaque one gives the fill colour.
+ * RGBA with fill count f and outline count v: a = (255 v + 2) >> 2,
+ * a_f = (255 f + 2) >> 2, A = (255 a + a_f (255 - a) + 127) / 255, each
+ * channel (line a 255 + fill a_f (255 - a) + 127 A) / (255 A); for f = 4 this
+ * is the HV_MODE_RGBA formula above, for f = 0 the unfilled one. */
+enum { HV_FILL_AA = 1 };
+typedef struct hv_fill_style {
+    uint32_t flags;              /* HV_FILL_AA or 0 */
+    uint32_t pattern_w, pattern_h;  /* 0, 0: no pattern */
+    const uint8_t* pattern_rgba; /* host memory, pattern_w * pattern_h * 4 bytes
+                                    (copied at the call) */
+} hv_fill_style;
+
 /* hv_build_opts.learned_hidden value: train no MLP residual. */
 #define HV_LEARNED_NO_MLP 0xFFFFFFFFu
 
@@ -118,8 +140,19 @@ typedef struct hv_build_opts {
     uint32_t learned_seed;       /* initialisation seed */
     uint32_t max_error;          /* accept the learned index only if its
                                     position error bound is <= this (0 = 4096) */
-    uint32_t reserved[3];
+    uint32_t object_placement;   /* HV_PLACE_DEVICE (0) or HV_PLACE_HOST */
+    uint32_t reserved[2];
 } hv_build_opts;
+
+/* hv_build_opts.object_placement.  HV_PLACE_HOST keeps the layer's index
+ * records (points, segment pieces; for polygon layers also the edges in
+ * polygon order) in pinned host memory after the build, mapped into the
+ * device's address space: the kernels read them over the CPU-GPU link
+ * (NVLink-C2C on GB300) while the tree nodes, keys and learned model stay in
+ * device memory.  For layers whose records do not fit the device (the
+ * paper's layers are read from memory-mapped index files, Sec. 4).  A layer
+ * file loaded back holds its records in device memory again. */
+enum { HV_PLACE_DEVICE = 0, HV_PLACE_HOST = 1 };
 
 typedef struct hv_layer_info {
     uint32_t kind;               /* HV_LAYER_* */
@@ -148,6 +181,8 @@ typedef struct hv_layer_info {
                                       segment pieces) */
     double learned_mean_window;    /* mean per-piece error bound (search window) */
     double learned_mean_window_linear;  /* ... of the linear pieces alone */
+    uint64_t host_bytes;           /* pinned host memory held by the layer
+                                      (HV_PLACE_HOST) */
 } hv_layer_info;
 
 /* ---- context ------------------------------------------------------------ */
@@ -160,6 +195,27 @@ int hv_destroy(hv_ctx* ctx);
 const char* hv_last_error(void);
 /* Bytes currently held by the context on its device. */
 int hv_ctx_device_bytes(hv_ctx* ctx, uint64_t* out);
+
+/* ---- quantisation (host only) ------------------------------------------- */
+
+/* Longitude / latitude in degrees (WGS 84, interleaved lon, lat; n pairs,
+ * host memory) -> grid coordinates (interleaved x, y; host memory): the
+ * spherical Web-Mercator projection the tile pyramid is defined in (Sec. 3.2,
+ * resolution(Z) in Web-Mercator metres), u = (lon + 180) / 360 and
+ * v = 1/2 - asinh(tan lat) / (2 pi) (v = 0 at the north edge), each scaled
+ * by 2^31, floored and shifted by -2^30; the east and south edges (u or
+ * v = 1) fall into the last grid unit.  lon outside [-180, 180] or |lat| above
+ * atan(sinh pi) = 85.0511287798... degrees (+1e-9, for the rounding of a
+ * caller's own copy; not a number counts as outside) -> HV_ERANGE,
+ * nothing written.  Floating point: outside the exact contract of the
+ * rendering, which starts from the grid integers. */
+int hv_lonlat_to_grid(const double* lonlat, uint64_t n, int32_t* xy);
+
+/* Tile router for replicas on several GPUs (every GPU holds the layers; a
+ * tile goes to one of them): rank_out[i] = the rank in 0..n_ranks-1 of request
+ * i, a hash of its (layer, z, x, y) -- the same tile always goes to the same
+ * rank, whatever its radius or mode, and tiles spread evenly.  Host only. */
+int hv_route_tiles(const hv_tile_req* reqs, uint64_t n, uint32_t n_ranks, uint32_t* rank_out);
 
 /* ---- layers (Sec. 3.1 data organisation; Sec. 4.1 Register Vector Data) -- */
 
@@ -225,15 +281,49 @@ uint64_t hv_tile_bytes(int mode);
  *   yields an all-zero tile and sets a sticky flag read by
  *   hv_layer_take_status().
  * out: host or device.  When reqs and out are both device memory the call is
- *   asynchronous on `stream`.  Otherwise requests are staged and / or tiles
- *   are rendered into device scratch and copied back, and the call returns
- *   after the stream has synchronised.
+ *   asynchronous on `stream`.  Otherwise requests are staged, tiles for
+ *   pinned (page-locked) host memory are written by the kernels straight into
+ *   it over the CPU-GPU link, tiles for other host memory are rendered into
+ *   device scratch and copied back, and the call returns after the stream has
+ *   synchronised.
  * style: colours for HV_MODE_RGBA (may be NULL otherwise).
  * Tiles that the layer cannot reach are written as zeros without index work
  * (Sec. 4.1, Parse Tasks). */
 int hv_render_tiles(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode,
                     int index_kind, const hv_style* style, void* out, uint64_t out_bytes,
                     void* stream);
+
+/* ---- display-driven buffer and overlay analysis (HiBuffer, HiBO; Sec. 2.3,
+ *      Sec. 3.2: the widths of Algorithm 1 as a buffer distance) ---------- */
+
+/* hv_render_tiles with the distance given on the ground instead of in
+ * pixels: every tile decides its samples against R = radius_units grid units
+ * (0..2^29, else HV_ERANGE), whatever its zoom, so the result is the buffer of
+ * the layer's objects at that distance (a polygon layer's buffer also holds
+ * its interiors) as seen in the tile.  The requests' r16 fields are ignored;
+ * everything else is as in hv_render_tiles. */
+int hv_render_buffer(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode, int index_kind,
+                     int32_t radius_units, const hv_style* style, void* out, uint64_t out_bytes, void* stream);
+
+/* Overlay operations on two buffers A and B, per pixel centre. */
+enum { HV_OVERLAY_AND = 0, HV_OVERLAY_OR = 1, HV_OVERLAY_XOR = 2, HV_OVERLAY_DIFF = 3 /* A and not B */ };
+
+/* Overlay of two buffers (HiBO): the MASK tiles of layer_a's buffer at
+ * radius_a and of layer_b's at radius_b (grid units, as hv_render_buffer),
+ * combined bit by bit with `op`.  The layers belong to one context; `out` is
+ * device memory of n * hv_tile_bytes(HV_MODE_MASK) bytes; reqs host or
+ * device.  The second buffer is rendered into scratch of the context, and
+ * the call returns after `stream` has synchronised. */
+int hv_overlay_tiles(hv_layer* layer_a, int32_t radius_a, hv_layer* layer_b, int32_t radius_b, int op,
+                     const hv_tile_req* reqs, uint32_t n, int index_kind, void* out, uint64_t out_bytes,
+                     void* stream);
+
+/* hv_render_tiles with a fill style for polygon layers (NULL fill: as
+ * hv_render_tiles; other layer kinds ignore it).  A pattern larger than
+ * 16 x 16 or with a texel alpha other than 0 and 255 -> HV_EINVAL. */
+int hv_render_tiles_styled(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode, int index_kind,
+                           const hv_style* style, const hv_fill_style* fill, void* out, uint64_t out_bytes,
+                           void* stream);
 
 /* Read and clear the layer's sticky device status (bit 0: an invalid device
  * request was seen; bit 1: an internal bounds check in the render kernel
@@ -255,7 +345,8 @@ int hv_render_tiles_counted(hv_layer* layer, const hv_tile_req* reqs, uint32_t n
                             int64_t* log, uint64_t log_cap, int64_t* log_count, void* stream);
 
 /* Phase profile counters of hv_render_tiles_phases (indices into its array;
- * a polygon layer's fill launch uses a second set at HV_PHASE_COUNT + i). */
+ * a polygon layer profiles its fill launch in the first set and its outline
+ * launch in a second set at HV_PHASE_COUNT + i). */
 enum {
     HV_PHASE_TOTAL = 0,       /* warp-cycles of the launch (CTA lifetimes x warps) */
     HV_PHASE_PROLOGUE,        /* request decode, result init (fill: outline decode) */
@@ -287,9 +378,50 @@ int hv_render_tiles_phases(hv_layer* layer, const hv_tile_req* reqs, uint32_t n,
                            uint64_t* phases, void* stream);
 
 /* Number of kernels hv_render_tiles launches per call (for launch accounting):
- * 1 for point and linestring layers, 2 for polygon layers (outline, then
- * fill); a call with host buffers launches that many per chunk of tiles. */
+ * 1 for point and linestring layers, 2 for polygon layers (fill, then
+ * outline); a call with host buffers launches that many per chunk of tiles. */
 int hv_render_launches(hv_layer* layer, int index_kind, uint32_t* launches);
+
+/* ---- result pool (Sec. 4.2 IMMF Result Pool; Sec. 4.1 Parse Tasks) ------ */
+
+/* A key-value store of rendered tiles in host memory: key (layer, z, x, y,
+ * r16, mode of an hv_tile_req, and the style's colours for HV_MODE_RGBA),
+ * value the tile's bytes.  Bounded by a byte capacity (the least recently
+ * used entries are evicted to make room) and an optional time to live
+ * (entries older than it are dropped when met).  Thread-safe.  The server
+ * consults it when a request is submitted (a hit completes the request
+ * without GPU work, as Parse Tasks drops already rendered tiles) and stores
+ * every tile it renders; measurement runs leave it off. */
+typedef struct hv_result_pool hv_result_pool;
+
+typedef struct hv_pool_stats {
+    uint64_t hits;          /* lookups answered from the pool */
+    uint64_t misses;        /* lookups not answered (absent or expired) */
+    uint64_t inserts;       /* tiles stored */
+    uint64_t evictions;     /* entries dropped to make room (least recently used first) */
+    uint64_t expirations;   /* entries dropped because they outlived the time to live */
+    uint64_t rejected;      /* tiles larger than the whole capacity (not stored) */
+    uint64_t entries;       /* entries held now */
+    uint64_t bytes;         /* tile bytes held now */
+    uint64_t capacity;      /* the byte capacity */
+} hv_pool_stats;
+
+/* capacity_bytes > 0; ttl_ms = 0: entries never expire. */
+int hv_result_pool_create(uint64_t capacity_bytes, uint32_t ttl_ms, hv_result_pool** out);
+int hv_result_pool_destroy(hv_result_pool* pool);
+/* Store a copy of `bytes` bytes of host memory `data` as the tile of `req`
+ * (its layer, z, x, y, r16 and mode fields) in `style` (may be NULL; used
+ * for HV_MODE_RGBA only); replaces an entry of the same key.  HV_ENOMEM if
+ * the tile alone exceeds the capacity. */
+int hv_result_pool_put(hv_result_pool* pool, const hv_tile_req* req, const hv_style* style,
+                       const void* data, uint64_t bytes);
+/* Look a tile up: on a hit copy it to `out` (host memory, out_bytes at least
+ * the tile's size) and set *hit = 1, else *hit = 0. */
+int hv_result_pool_get(hv_result_pool* pool, const hv_tile_req* req, const hv_style* style, void* out,
+                       uint64_t out_bytes, uint32_t* hit);
+int hv_result_pool_stats(hv_result_pool* pool, hv_pool_stats* out);
+/* Drop every entry (the counters are kept). */
+int hv_result_pool_clear(hv_result_pool* pool);
 
 /* ---- serving (Sec. 4: MTVS task pool, IMMF, HPVE as one GPU loop) ------ */
 
@@ -313,6 +445,9 @@ typedef struct hv_server_opts {
                                   built; else the R-tree */
     uint32_t use_graphs;       /* launch batches as captured CUDA graphs */
     hv_style style;
+    hv_result_pool* pool;      /* NULL: no result pool; else consulted at
+                                  submission and filled with every rendered
+                                  tile (the pool must outlive the server) */
 } hv_server_opts;
 
 typedef struct hv_done {
@@ -343,9 +478,22 @@ int hv_server_stop(hv_server* srv);
  * concurrently. */
 int hv_server_replay(hv_server* srv, const hv_tile_req* reqs, const double* arrival_us, uint64_t n,
                      double* latency_us, double* wall_us);
+/* hv_server_replay that also writes each request's latency in parts
+ * (microseconds): parts_us[4i .. 4i+3] = wait before submission (queue
+ * full), wait in the task pool (submission -> its batch is launched),
+ * service (launch -> the worker sees the batch complete: copies and
+ * kernels), hand-out (completion -> the replay's poll).  The first three sum
+ * to latency_us[i] up to clock reads. */
+int hv_server_replay_detail(hv_server* srv, const hv_tile_req* reqs, const double* arrival_us, uint64_t n,
+                            double* latency_us, double* parts_us, double* wall_us);
 /* Counters: batches launched, tiles launched, graph launches, slots. */
 int hv_server_stats(hv_server* srv, uint64_t* batches, uint64_t* tiles, uint64_t* graph_launches,
                     uint32_t* slots);
+/* Requests completed at submission without GPU work (Sec. 4.1 Parse Tasks):
+ * answered by the result pool, and tiles that the layer cannot reach (its
+ * objects' box, widened by the request's radius, misses the tile), which
+ * are all zero. */
+int hv_server_shortcuts(hv_server* srv, uint64_t* pool_hits, uint64_t* empty_tiles);
 
 /* ---- rendering without allocation (no counterpart in the paper) --------- */
 

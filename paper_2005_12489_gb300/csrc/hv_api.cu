@@ -1,5 +1,6 @@
 // The C ABI: contexts, layer registration (HiVision Sec. 4.1, Register Vector
 // Data), index builds and tile rendering (Sec. 4.1, Parse Tasks / Render Tiles).
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -51,6 +52,17 @@ void dev_free(Ctx* c, void* p, uint64_t bytes) {
     cudaFree(p);
     std::lock_guard<std::mutex> g(c->mu);
     c->held -= std::min(c->held, bytes);
+}
+
+// The device address of pinned (page-locked) host memory, or NULL for other
+// memory: pinned host memory is mapped into the device's address space.
+static void* pinned_device_view(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 // Is `p` device-accessible memory that is not host memory?
@@ -132,11 +144,17 @@ Layer* new_layer(Ctx* c, int kind) {
 
 void free_layer(Layer* L) {
     Ctx* c = L->ctx;
-    dev_free(c, L->obj, L->obj_bytes);
+    if (L->obj_host)
+        cudaFreeHost(L->obj_host);
+    else
+        dev_free(c, L->obj, L->obj_bytes);
     if (L->keys) dev_free(c, L->keys, L->n_obj * 8);
     free_tree(c, &L->tree);
     if (L->kind == HV_LAYER_POLYGONS) {
-        dev_free(c, L->poly_edges, (L->n_src ? L->n_src : 1) * 16);
+        if (L->edges_host)
+            cudaFreeHost(L->edges_host);
+        else
+            dev_free(c, L->poly_edges, (L->n_src ? L->n_src : 1) * 16);
         dev_free(c, L->poly_edge_off, (L->n_poly + 1) * 8);
         dev_free(c, L->mbr_obj, (L->n_poly ? L->n_poly : 1) * 16);
         if (L->mbr_ids) dev_free(c, L->mbr_ids, L->n_poly * 4);
@@ -211,6 +229,7 @@ int hv_destroy(hv_ctx* ctx) {
     cudaSetDevice(c->device);
     if (c->req_buf) dev_free(c, c->req_buf, c->req_cap);
     if (c->out_buf) dev_free(c, c->out_buf, c->out_cap);
+    if (c->overlay_buf) dev_free(c, c->overlay_buf, c->overlay_cap);
     if (c->pinned_req) cudaFreeHost(c->pinned_req);
     for (int k = 0; k < 2; k++) {
         if (c->ev_rendered[k]) cudaEventDestroy(c->ev_rendered[k]);
@@ -218,6 +237,47 @@ int hv_destroy(hv_ctx* ctx) {
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     delete c;
+    return HV_OK;
+}
+
+int hv_lonlat_to_grid(const double* lonlat, uint64_t n, int32_t* xy) {
+    if (n && (!lonlat || !xy)) { set_error("hv_lonlat_to_grid: NULL argument"); return HV_EINVAL; }
+    const double kPi = 3.14159265358979323846;
+    // atan(sinh(pi)) in degrees, with room for the rounding of a caller's own copy
+    const double lat_max = atan(sinh(kPi)) * 180.0 / kPi + 1e-9;
+    for (uint64_t i = 0; i < n; i++) {
+        const double lon = lonlat[2 * i], lat = lonlat[2 * i + 1];
+        if (!(lon >= -180.0 && lon <= 180.0 && lat >= -lat_max && lat <= lat_max)) {
+            set_error("hv_lonlat_to_grid: point %llu (%g, %g) outside the Web-Mercator square",
+                      (unsigned long long)i, lon, lat);
+            return HV_ERANGE;
+        }
+    }
+    const double scale = 2147483648.0;   // 2^31 grid units per axis
+    for (uint64_t i = 0; i < n; i++) {
+        const double u = (lonlat[2 * i] + 180.0) / 360.0;
+        const double v = 0.5 - asinh(tan(lonlat[2 * i + 1] * kPi / 180.0)) / (2.0 * kPi);
+        const int64_t gx = (int64_t)floor(u * scale) - kGridHalf, gy = (int64_t)floor(v * scale) - kGridHalf;
+        xy[2 * i] = (int32_t)std::min<int64_t>(std::max<int64_t>(gx, -kGridHalf), kGridHalf - 1);
+        xy[2 * i + 1] = (int32_t)std::min<int64_t>(std::max<int64_t>(gy, -kGridHalf), kGridHalf - 1);
+    }
+    return HV_OK;
+}
+
+int hv_route_tiles(const hv_tile_req* reqs, uint64_t n, uint32_t n_ranks, uint32_t* rank_out) {
+    if ((n && (!reqs || !rank_out)) || n_ranks == 0) { set_error("hv_route_tiles: bad arguments"); return HV_EINVAL; }
+    for (uint64_t i = 0; i < n; i++) {
+        const hv_tile_req& q = reqs[i];
+        // a unique key per tile (x, y < 2^20 at z <= 19), mixed (splitmix64),
+        // then scaled to the ranks by the high half of a 64 x 32-bit product
+        uint64_t h = ((uint64_t)q.layer << 45) ^ ((uint64_t)(q.z & 31) << 40) ^ ((uint64_t)(q.x & 0xFFFFF) << 20) ^
+                     (uint64_t)(q.y & 0xFFFFF);
+        h += 0x9E3779B97F4A7C15ull;
+        h = (h ^ (h >> 30)) * 0xBF58476D1CE4E5B9ull;
+        h = (h ^ (h >> 27)) * 0x94D049BB133111EBull;
+        h ^= h >> 31;
+        rank_out[i] = (uint32_t)(((h >> 32) * (uint64_t)n_ranks) >> 32);
+    }
     return HV_OK;
 }
 
@@ -286,6 +346,37 @@ int hv_layer_load_polygons(hv_ctx* ctx, const int32_t* xy, uint64_t n_vert, cons
     return finish_layer(L, out);
 }
 
+}  // extern "C"
+
+namespace hv {
+
+// Move a device array into mapped pinned host memory; *p becomes its device
+// address (read over the CPU-GPU link), *host its host address.
+static int move_to_host(Ctx* c, void** p, uint64_t bytes, void** host) {
+    void* h = nullptr;
+    void* d = nullptr;
+    if (cudaHostAlloc(&h, bytes ? bytes : 16, cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("pinned host allocation of %llu bytes failed", (unsigned long long)bytes);
+        return HV_ENOMEM;
+    }
+    cudaError_t e = cudaHostGetDevicePointer(&d, h, 0);
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(h, *p, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cudaFreeHost(h);
+        set_error("moving %llu bytes to host memory: %s", (unsigned long long)bytes, cudaGetErrorString(e));
+        return HV_ECUDA;
+    }
+    dev_free(c, *p, bytes);
+    *p = d;
+    *host = h;
+    return HV_OK;
+}
+
+}  // namespace hv
+
+extern "C" {
+
 int hv_layer_build_index(hv_layer* layer, uint32_t kinds, const hv_build_opts* opts) {
     if (!layer) { set_error("hv_layer_build_index: NULL layer"); return HV_EINVAL; }
     if (kinds & ~(uint32_t)(HV_INDEX_RTREE | HV_INDEX_LEARNED)) { set_error("unknown index kind"); return HV_EINVAL; }
@@ -313,6 +404,15 @@ int hv_layer_build_index(hv_layer* layer, uint32_t kinds, const hv_build_opts* o
     if ((kinds & HV_INDEX_LEARNED) && !(L->indexes & HV_INDEX_LEARNED)) {
         HV_TRY(build_learned(L, opts));
         L->indexes |= HV_INDEX_LEARNED;
+    }
+    if (opts && opts->object_placement == HV_PLACE_HOST) {
+        HV_CUDA(cudaDeviceSynchronize());
+        if (!L->obj_host && L->obj) HV_TRY(move_to_host(L->ctx, &L->obj, L->obj_bytes, &L->obj_host));
+        if (L->kind == HV_LAYER_POLYGONS && !L->edges_host && L->poly_edges)
+            HV_TRY(move_to_host(L->ctx, (void**)&L->poly_edges, (L->n_src ? L->n_src : 1) * 16, &L->edges_host));
+    } else if (opts && opts->object_placement != HV_PLACE_DEVICE) {
+        set_error("hv_layer_build_index: unknown object placement %u", opts->object_placement);
+        return HV_EINVAL;
     }
     return HV_OK;
 }
@@ -347,9 +447,11 @@ int hv_layer_info_get(hv_layer* layer, hv_layer_info* out) {
         out->learned_mean_window_linear = lv.mean_window_linear;
         out->learned_halo = lv.halo;
     }
-    uint64_t bytes = L->obj_bytes + (L->keys ? L->n_obj * 8 : 0) + L->tree.nodes_bytes;
+    uint64_t bytes = (L->obj_host ? 0 : L->obj_bytes) + (L->keys ? L->n_obj * 8 : 0) + L->tree.nodes_bytes;
     if (L->kind == HV_LAYER_POLYGONS)
-        bytes += L->n_src * 16 + (L->n_poly + 1) * 8 + L->n_poly * (16 + 4 + 8) + L->mbr_tree.nodes_bytes;
+        bytes += (L->edges_host ? 0 : L->n_src * 16) + (L->n_poly + 1) * 8 + L->n_poly * (16 + 4 + 8) +
+                 L->mbr_tree.nodes_bytes;
+    out->host_bytes = (L->obj_host ? L->obj_bytes : 0) + (L->edges_host ? L->n_src * 16 : 0);
     for (auto& a : L->learned.allocs) bytes += a.second;
     for (auto& a : L->mbr_learned.allocs) bytes += a.second;
     out->device_bytes = bytes;
@@ -365,8 +467,15 @@ int hv_layer_free(hv_layer* layer) {
     return HV_OK;
 }
 
-int hv_render_tiles(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode, int index_kind,
-                    const hv_style* style, void* out, uint64_t out_bytes, void* stream) {
+}  // extern "C"
+
+namespace hv {
+
+// hv_render_tiles and hv_render_buffer: R_units < 0 takes each request's
+// radius r16 (R = r16 * 2^(19 - z)), else R = R_units for every tile.
+static int render_impl(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode, int index_kind,
+                       const hv_style* style, void* out, uint64_t out_bytes, void* stream, int32_t R_units,
+                       const hv_fill_style* fill = nullptr) {
     if (!layer) { set_error("hv_render_tiles: NULL layer"); return HV_EINVAL; }
     Layer* L = (Layer*)layer;
     uint64_t tb = hv_tile_bytes(mode);
@@ -384,22 +493,31 @@ int hv_render_tiles(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mo
         return HV_EINVAL;
     }
     if (((uintptr_t)out & 15u) != 0) { set_error("hv_render_tiles: out must be 16-byte aligned"); return HV_EINVAL; }
+    if (!fill_style_ok(fill)) {
+        set_error("hv_render_tiles_styled: invalid fill style (flags, pattern size 1..16, texel alpha 0 or 255)");
+        return HV_EINVAL;
+    }
     Ctx* c = L->ctx;
     HV_CUDA(cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream;
     bool dev_reqs = is_device_ptr(reqs);
     bool dev_out = is_device_ptr(out);
+    // pinned host output: the kernels write the tiles straight into it over
+    // the CPU-GPU link (NVLink-C2C), no staging and no copies
+    void* pinned_out = dev_out ? nullptr : pinned_device_view(out);
     if (!dev_reqs) {
         for (uint32_t k = 0; k < n; k++) {
             const hv_tile_req& q = reqs[k];
-            if (q.z > 19 || q.x >= (1u << q.z) || q.y >= (1u << q.z) || q.r16 < 1 || q.r16 > 1024) {
+            if (q.z > 19 || q.x >= (1u << q.z) || q.y >= (1u << q.z) ||
+                (R_units < 0 && (q.r16 < 1 || q.r16 > 1024))) {
                 set_error("hv_render_tiles: request %u (z=%u x=%u y=%u r16=%u) out of range", k, q.z, q.x,
                           q.y, q.r16);
                 return HV_ERANGE;
             }
         }
     }
-    if (dev_reqs && dev_out) return launch_render(L, reqs, n, mode, index_kind, style, (uint8_t*)out, st);
+    if (dev_reqs && dev_out)
+        return launch_render(L, reqs, n, mode, index_kind, style, (uint8_t*)out, st, nullptr, nullptr, R_units, fill);
     std::lock_guard<std::mutex> g(c->render_mu);
     const hv_tile_req* d_reqs = reqs;
     if (!dev_reqs) {
@@ -408,9 +526,11 @@ int hv_render_tiles(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mo
         HV_CUDA(cudaMemcpyAsync(c->req_buf, reqs, rb, cudaMemcpyHostToDevice, st));
         d_reqs = (const hv_tile_req*)c->req_buf;
     }
-    if (dev_out) {
-        HV_TRY(launch_render(L, d_reqs, n, mode, index_kind, style, (uint8_t*)out, st));
-        // the request staging must be consumed before the next call reuses it
+    if (dev_out || pinned_out) {
+        HV_TRY(launch_render(L, d_reqs, n, mode, index_kind, style, (uint8_t*)(dev_out ? out : pinned_out), st,
+                             nullptr, nullptr, R_units, fill));
+        // the request staging must be consumed before the next call reuses
+        // it, and host output must be complete when the call returns
         HV_CUDA(cudaStreamSynchronize(st));
         return HV_OK;
     }
@@ -431,7 +551,8 @@ int hv_render_tiles(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mo
         uint32_t first = i * chunk, cnt = n - first < chunk ? n - first : chunk;
         int b = i & 1;
         HV_CUDA(cudaStreamWaitEvent(st, c->ev_copied[b], 0));   // buffer free
-        HV_TRY(launch_render(L, d_reqs + first, cnt, mode, index_kind, style, bufs[b], st));
+        HV_TRY(launch_render(L, d_reqs + first, cnt, mode, index_kind, style, bufs[b], st, nullptr, nullptr,
+                             R_units, fill));
         HV_CUDA(cudaEventRecord(c->ev_rendered[b], st));
         return HV_OK;
     };
@@ -450,6 +571,70 @@ int hv_render_tiles(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mo
     }
     HV_CUDA(cudaStreamSynchronize(c->copy_stream));
     HV_CUDA(cudaStreamSynchronize(st));
+    return HV_OK;
+}
+
+namespace {
+
+// Bitwise combination of two MASK results, word by word (overlay).
+__global__ void k_combine(uint32_t* a, const uint32_t* b, uint64_t n, int op) {
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t x = a[i], y = b[i];
+    a[i] = op == HV_OVERLAY_AND ? (x & y) : op == HV_OVERLAY_OR ? (x | y) : op == HV_OVERLAY_XOR ? (x ^ y) : (x & ~y);
+}
+
+}  // namespace
+
+}  // namespace hv
+
+extern "C" {
+
+int hv_render_tiles(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode, int index_kind,
+                    const hv_style* style, void* out, uint64_t out_bytes, void* stream) {
+    return render_impl(layer, reqs, n, mode, index_kind, style, out, out_bytes, stream, -1);
+}
+
+int hv_render_tiles_styled(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode, int index_kind,
+                           const hv_style* style, const hv_fill_style* fill, void* out, uint64_t out_bytes,
+                           void* stream) {
+    return render_impl(layer, reqs, n, mode, index_kind, style, out, out_bytes, stream, -1, fill);
+}
+
+int hv_render_buffer(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode, int index_kind,
+                     int32_t radius_units, const hv_style* style, void* out, uint64_t out_bytes, void* stream) {
+    if (radius_units < 0 || radius_units > kMaxBufferRadius) {
+        set_error("hv_render_buffer: radius %d outside 0..2^29 units", radius_units);
+        return HV_ERANGE;
+    }
+    return render_impl(layer, reqs, n, mode, index_kind, style, out, out_bytes, stream, radius_units);
+}
+
+int hv_overlay_tiles(hv_layer* layer_a, int32_t radius_a, hv_layer* layer_b, int32_t radius_b, int op,
+                     const hv_tile_req* reqs, uint32_t n, int index_kind, void* out, uint64_t out_bytes,
+                     void* stream) {
+    if (!layer_a || !layer_b) { set_error("hv_overlay_tiles: NULL layer"); return HV_EINVAL; }
+    if (op < HV_OVERLAY_AND || op > HV_OVERLAY_DIFF) { set_error("hv_overlay_tiles: unknown op %d", op); return HV_EINVAL; }
+    Layer* A = (Layer*)layer_a;
+    Layer* B = (Layer*)layer_b;
+    if (A->ctx != B->ctx) { set_error("hv_overlay_tiles: the layers belong to different contexts"); return HV_EINVAL; }
+    if (n == 0) return HV_OK;
+    if (!out || !is_device_ptr(out)) { set_error("hv_overlay_tiles: out must be device memory"); return HV_EINVAL; }
+    const uint64_t tb = hv_tile_bytes(HV_MODE_MASK);
+    if (out_bytes < (uint64_t)n * tb) { set_error("hv_overlay_tiles: out_bytes too small"); return HV_EINVAL; }
+    Ctx* c = A->ctx;
+    HV_CUDA(cudaSetDevice(c->device));
+    std::lock_guard<std::mutex> g(c->overlay_mu);
+    HV_TRY(grow(c, &c->overlay_buf, &c->overlay_cap, (uint64_t)n * tb));
+    HV_TRY(hv_render_buffer(layer_a, reqs, n, HV_MODE_MASK, index_kind, radius_a, nullptr, out, out_bytes, stream));
+    HV_TRY(hv_render_buffer(layer_b, reqs, n, HV_MODE_MASK, index_kind, radius_b, nullptr, c->overlay_buf,
+                            (uint64_t)n * tb, stream));
+    const uint64_t words = (uint64_t)n * tb / 4;
+    k_combine<<<(unsigned)((words + 255) / 256), 256, 0, (cudaStream_t)stream>>>((uint32_t*)out,
+                                                                                (const uint32_t*)c->overlay_buf, words, op);
+    HV_CUDA(cudaGetLastError());
+    // the scratch holds B's masks until the combine has read them
+    HV_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     return HV_OK;
 }
 

@@ -15,6 +15,7 @@ namespace hv {
 constexpr int kFanout = 32;        // children per inner node, objects per leaf
 constexpr int kMaxLevels = 16;     // inner levels of a tree (32^16 >> 2^64)
 constexpr int kTile = 256;         // tile side in pixels (Sec. 4)
+constexpr int32_t kMaxBufferRadius = 1 << 29;   // largest buffer radius (grid units)
 
 void set_error(const char* fmt, ...);
 
@@ -35,6 +36,9 @@ struct Ctx {
     cudaEvent_t ev_rendered[2] = {nullptr, nullptr};
     cudaEvent_t ev_copied[2] = {nullptr, nullptr};
     std::mutex render_mu;         // serialises use of the scratch above
+    void* overlay_buf = nullptr;  // the second layer's masks of an overlay
+    uint64_t overlay_cap = 0;
+    std::mutex overlay_mu;
 };
 
 int dev_alloc(Ctx* c, void** p, uint64_t bytes);
@@ -42,6 +46,10 @@ void dev_free(Ctx* c, void* p, uint64_t bytes);
 
 // A segment piece: the whole segment (for the exact distance test) and a
 // conservative box of the part of it the piece stands for (for pruning).
+// Stored as 32-byte records: a leaf visit loads both halves at once (a
+// layout with the boxes and the segments in two arrays, the segment read only
+// by lanes whose box is in reach, measured slower: the dependent second load
+// costs more latency than the bytes it saves).
 struct __align__(16) Piece {
     int4 seg;
     int4 box;
@@ -136,6 +144,9 @@ struct Layer {
     Learned learned;                 // over obj
     Learned mbr_learned;             // over polygon boxes
     int4 mbr = {0, 0, -1, -1};
+    // HV_PLACE_HOST: obj (and poly_edges) live in mapped pinned host memory
+    void* obj_host = nullptr;        // host address of obj (NULL: device memory)
+    void* edges_host = nullptr;      // host address of poly_edges (NULL: device memory)
     uint32_t* status = nullptr;      // sticky device status word
     double build_ms = 0;
     std::vector<std::pair<void*, uint64_t>> extra;  // other allocations
@@ -159,10 +170,20 @@ struct RenderLog {
     int64_t* count;
     uint64_t* phases = nullptr;   // phase profile counters (instrumented launch)
 };
+// R_units < 0: each request's radius r16 * 2^(19 - z); else the radius of
+// every tile in grid units (buffer analysis), at most kMaxBufferRadius.
 int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int index_kind,
                   const hv_style* style, uint8_t* d_out, cudaStream_t stream,
-                  const RenderLog* log = nullptr, const uint32_t* n_dev = nullptr);
+                  const RenderLog* log = nullptr, const uint32_t* n_dev = nullptr, int32_t R_units = -1,
+                  const hv_fill_style* fill = nullptr);
+// A fill style is valid: HV_FILL_AA or 0, and a pattern of at most 16 x 16
+// texels with alpha 0 or 255 (or none).
+bool fill_style_ok(const hv_fill_style* fill);
 uint32_t render_launch_count(Layer* L, int index_kind);
+// result pool (hv_pool.cu)
+struct ResultPool;
+bool pool_lookup(ResultPool* P, const hv_tile_req& r, const hv_style* style, std::vector<uint8_t>* out);
+int pool_insert(ResultPool* P, const hv_tile_req& r, const hv_style* style, const void* data, uint64_t n);
 
 }  // namespace hv
 

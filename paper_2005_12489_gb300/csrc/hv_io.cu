@@ -65,7 +65,7 @@ struct Writer {
             uint64_t b = bytes - o < kStage ? bytes - o : kStage;
             const void* src = (const uint8_t*)p + o;
             if (device) {
-                if (cudaMemcpy(stage, src, b, cudaMemcpyDeviceToHost) != cudaSuccess) { ok = false; break; }
+                if (cudaMemcpy(stage, src, b, cudaMemcpyDefault) != cudaSuccess) { ok = false; break; }
                 src = stage;
             }
             ok = fwrite(src, 1, b, f) == b;

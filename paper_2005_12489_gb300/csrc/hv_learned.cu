@@ -524,7 +524,7 @@ int build_learned(Layer* L, const hv_build_opts* opts) {
     uint32_t max_err = opts && opts->max_error ? opts->max_error : 4096;
     int64_t e1 = 0, e2 = 0;
     // segment pieces: their boxes follow each segment in the record, and the
-    // bounded piece extent makes every record fit the halo
+    // bounded piece extent makes every record fit the halo (no side tree)
     const int4* piece_boxes = L->kind == HV_LAYER_POINTS ? nullptr : (const int4*)L->obj + 1;
     HV_TRY(build_one(c, &L->learned, L->keys, L->n_obj, piece_boxes, 2, false, nullptr, opts, &e1));
     if (L->kind == HV_LAYER_POLYGONS)

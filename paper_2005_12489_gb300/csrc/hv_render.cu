@@ -40,9 +40,13 @@ constexpr int kBlocksX = kTile / kBW;
 constexpr int kFCap = 512;
 constexpr int kBucketCap = 2048;   // keeps the static shared memory under 48 KiB
 constexpr int kCullCells = 64;     // learned cull: at most this many Hilbert cells per strip
+constexpr int kMaxPattern = 16;    // fill patterns: at most 16 x 16 texels
 
-// result bits per pixel
+// result bits per pixel: bits 0-3 the outline's super-samples, bit 4 the
+// centre, bits 5-7 the fill field (0: not filled; centre fill: 1; the
+// anti-aliased fill: the number of super-samples inside, 0..4)
 constexpr uint32_t kResCentre = 16u, kResFill = 32u;
+constexpr int kResFillShift = 5;
 
 struct TreeArg {
     const int32_t* nodes;
@@ -78,6 +82,12 @@ struct Params {
     // learned candidate lookup (use_learned): models over the sorted keys of
     // the objects and of the polygon boxes, their halos and side trees
     int use_learned;
+    int32_t R_units;            // >= 0: the radius of every tile (buffer analysis), else from r16
+    // polygon fill style: anti-aliased fill, and a pattern of pat_w x pat_h
+    // RGBA texels (0: none) laid over the global pixel grid
+    int fill_aa;
+    int pat_w, pat_h;
+    uchar4 pattern[kMaxPattern * kMaxPattern];
     LModel lm, mlm;
     int32_t halo, mhalo;
     TreeArg side, mside;
@@ -351,7 +361,9 @@ __device__ __forceinline__ uint32_t line_lanes(const Lane& s, int32_t px, int32_
 // orientation num(c) = dx (y - ly) - (x_c - lx) dy of the edge ordered by y
 // falls as the column c grows, so the crossed columns are a prefix 0..t-1,
 // t found by a three-step binary search with exact 64-bit products.
-__device__ __forceinline__ uint32_t crossing_columns(int4 e, const Lane& s) {
+// (ox, oy) offsets the samples from the pixel centres (the anti-aliased
+// fill's super-samples); the column search is the same.
+__device__ __forceinline__ uint32_t crossing_columns(int4 e, const Lane& s, int32_t ox = 0, int32_t oy = 0) {
     int32_t lx = e.x, ly = e.y, hx = e.z, hy = e.w;
     if (ly > hy) {
         lx = e.z; ly = e.w; hx = e.x; hy = e.y;
@@ -361,9 +373,9 @@ __device__ __forceinline__ uint32_t crossing_columns(int4 e, const Lane& s) {
     uint32_t m = 0u;
 #pragma unroll
     for (int r = 0; r < kBH; r++) {
-        const int32_t y = s.by0 + (r << s.L);
+        const int32_t y = s.by0 + (r << s.L) + oy;
         if (y < ly || y >= hy) continue;
-        const int64_t n0 = (int64_t)ex * (y - ly) - (int64_t)(s.bx0 - lx) * ey;
+        const int64_t n0 = (int64_t)ex * (y - ly) - ((int64_t)s.bx0 + ox - lx) * ey;
         // column c is crossed iff n0 > c ps ey
         int t = n0 > (int64_t)(3 << s.L) * ey ? 4 : 0;
         if (n0 > (int64_t)((t + 1) << s.L) * ey) t += 2;
@@ -517,7 +529,10 @@ struct FillLeaf {
             int32_t bx0 = __shfl_sync(kFull, b.x, k), by0 = __shfl_sync(kFull, b.y, k);
             int32_t bx1 = __shfl_sync(kFull, b.z, k), by1 = __shfl_sync(kFull, b.w, k);
             uint32_t pid = __shfl_sync(kFull, id, k);
-            bool active = s.und && s.cx >= bx0 && s.cx <= bx1 && s.cy >= by0 && s.cy <= by1;
+            // a sample of the lane (the centre, or a super-sample within off
+            // of it) may lie in the box
+            bool active = s.und && s.cx + s.off >= bx0 && s.cx - s.off <= bx1 && s.cy + s.off >= by0 &&
+                          s.cy - s.off <= by1;
             if (__ballot_sync(kFull, active) == 0) continue;
             log_read(p, kLogPoly, pid, lane);
             if (pid >= p.n_poly) {
@@ -530,15 +545,31 @@ struct FillLeaf {
                 continue;
             }
             // each lane takes an edge; the crossed pixels of all the edges,
-            // XOR-reduced, are every pixel's parity at once
-            uint32_t par = 0u;
-            for (uint64_t base = e0; base < e1; base += 32) {
-                uint32_t cm = 0u;
-                if (base + lane < e1) cm = crossing_columns(__ldg(p.poly_edges + base + lane), s);
-                par ^= __reduce_xor_sync(kFull, cm);
+            // XOR-reduced, are every pixel's parity at once (per sample)
+            uint32_t inside = 0u;
+            if (s.nk == 1) {
+                uint32_t par = 0u;
+                for (uint64_t base = e0; base < e1; base += 32) {
+                    uint32_t cm = 0u;
+                    if (base + lane < e1) cm = crossing_columns(__ldg(p.poly_edges + base + lane), s);
+                    par ^= __reduce_xor_sync(kFull, cm);
+                }
+                inside = (par >> lane) & 1u;
+            } else {
+                // super-sample k sits at -+off in x (bit 0) and y (bit 1)
+                uint32_t par[4] = {0u, 0u, 0u, 0u};
+                for (uint64_t base = e0; base < e1; base += 32) {
+                    int4 e = make_int4(0, 0, 0, 0);   // a level edge crosses nothing
+                    if (base + lane < e1) e = __ldg(p.poly_edges + base + lane);
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        par[k] ^= __reduce_xor_sync(kFull, crossing_columns(e, s, (k & 1) ? s.off : -s.off,
+                                                                            (k & 2) ? s.off : -s.off));
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) inside |= ((par[k] >> lane) & 1u) << k;
             }
-            const uint32_t parity = (par >> lane) & 1u;
-            if (active && parity) s.und = 0;
+            if (active) s.und &= ~inside;
             uint32_t U2 = __ballot_sync(kFull, s.und != 0);
             if (U2 != s.U) {
                 s.U = U2;
@@ -886,7 +917,7 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         s.bx0 = X0 + (bx * kBW) * ps + (ps >> 1);
         s.by0 = Y0 + (strip * p.rows + by * kBH) * ps + (ps >> 1);
         s.R2 = (int64_t)R * R;
-        if (V::kFill || mask_mode) {
+        if ((V::kFill && !(p.fill_aa && !mask_mode)) || mask_mode) {
             s.off = 0;
             s.und = 1u;
             s.nk = 1;
@@ -899,6 +930,13 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         s.q = q;
         s.U = kFull;
         for (int k = 0; k < 4; k++) s.Uk[k] = k < s.nk ? kFull : 0u;
+        if (!V::kFill && mask_mode && p.pat_w == 0) {
+            // a MASK pixel whose centre is already filled is decided (unless a
+            // pattern may leave it transparent)
+            const uint32_t open = __ballot_sync(kFull, (sm.res[jl * kTile + i] >> kResFillShift) == 0);
+            s.U = s.Uk[0] = open;
+            s.und = (open >> lane) & 1u;
+        }
         uint32_t und0 = s.und;
         {
             // this block's column list, or the whole frontier
@@ -955,7 +993,8 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         uint32_t covered = und0 & ~s.und;
         uint8_t r = sm.res[jl * kTile + i];
         if (V::kFill) {
-            if (covered) r |= kResFill;
+            // the centre (1), or the number of super-samples inside (0..4)
+            if (covered) r |= (s.nk == 1 ? 1u : (uint32_t)__popc(covered)) << kResFillShift;
         } else if (mask_mode) {
             if (covered) r |= kResCentre;
         } else {
@@ -990,7 +1029,8 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
         // the column lists are rebuilt for every pass, also for an empty
         // frontier (a strip reached only by the side tree), so that the
         // blocks never read the lists of an earlier stage
-        const int32_t off = (V::kFill || mask_mode) ? 0 : ((1 << (23 - z)) >> 2);
+        const bool sub = V::kFill ? (p.fill_aa && !mask_mode) : !mask_mode;   // super-samples
+        const int32_t off = sub ? ((1 << (23 - z)) >> 2) : 0;
         const long long t_bin = tick<kProf>();
         bin_frontier(sm, X0, 23 - z, (V::kFill ? 0 : R) + off, tid);
         if (tid == 0) prof_since<kProf>(sm, kPBin, t_bin, 0);
@@ -1005,11 +1045,14 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
 }
 
 // Kernel parts: one per layer kind, and polygon layers in two launches --
-// the outline (the HV_LAYER_POLYGONS part: Algorithm 1 over the edges,
-// encoded as if nothing were filled), then the fill (kPolyFill: Algorithm 2,
-// which reads the outline back from the output and composes the strip).
-// Apart, each part's traversal stays small enough for the instruction cache;
-// fused, the polygon kernel measured 40% slower.
+// first the fill (kPolyFill: Algorithm 2), which leaves the strip's fill bits
+// as a bit mask (MASK layout, 32 bytes per pixel row) at the start of the
+// strip's own part of the output, then the outline (the HV_LAYER_POLYGONS
+// part: Algorithm 1 over the edges), which reads those bits back, decides
+// the samples and encodes the composed strip over them.  Each CTA reads and
+// writes only its own strip's part of the output, so the bits never meet
+// another CTA's writes.  Apart, each part's traversal stays small enough for
+// the instruction cache; fused, the polygon kernel measured 40% slower.
 constexpr int kPolyFill = 3;
 
 // CTAs per SM: points keep four (their traversal fits 64 registers); the
@@ -1019,22 +1062,36 @@ struct KindTraits {
     static constexpr int kBlocksPerSM = kKind == HV_LAYER_POINTS ? 4 : 3;
 };
 
-// The polygon fill part starts from the outline part's output: per pixel the
-// centre bit (MASK), the coverage count v (COVERAGE), or v recovered from the
-// alpha (255 v + 2) >> 2 in {0, 64, 128, 191, 255} (RGBA); the strip's result
-// bytes get v sample bits (only their count is encoded) or the centre bit.
-__device__ void decode_outline(const Params& p, const uint8_t* out, Smem& sm, int rows, int strip, int tid) {
-    for (int k = tid; k < rows * kTile; k += kThreads) {
-        const int jl = k / kTile, i = k % kTile;
-        const uint64_t px = (uint64_t)(strip * rows + jl) * kTile + i;
-        uint8_t r;
-        if (p.mode == HV_MODE_MASK) {
-            r = ((out[px >> 3] >> (px & 7)) & 1u) ? (uint8_t)kResCentre : (uint8_t)0;
-        } else {
-            const uint32_t v = p.mode == HV_MODE_COVERAGE ? (out[px] & 7u) : ((out[4 * px + 3] + 32u) >> 6);
-            r = (uint8_t)((1u << v) - 1u);
+// The pattern texel of global pixel (gx, gy).
+__device__ __forceinline__ uchar4 fill_texel(const Params& p, uint32_t gx, uint32_t gy) {
+    return p.pattern[(gy % (uint32_t)p.pat_h) * (uint32_t)p.pat_w + gx % (uint32_t)p.pat_w];
+}
+
+// Byte offset of a strip's part of a tile's output (rows x the bytes of a
+// pixel row in the mode), which holds at least rows x 32 bytes.
+__device__ __forceinline__ uint64_t strip_offset(int mode, int rows, int strip) {
+    const uint64_t row_bytes = mode == HV_MODE_MASK ? kTile / 8 : (mode == HV_MODE_COVERAGE ? kTile : 4 * kTile);
+    return (uint64_t)strip * rows * row_bytes;
+}
+
+// The outline part of a polygon layer starts from the fill part's results:
+// a bit per pixel (centre fill), or with the anti-aliased fill a byte per
+// pixel holding the number of super-samples inside.
+__device__ void decode_fill(const uint8_t* region, Smem& sm, int rows, int tid, bool aa_bytes) {
+    if (aa_bytes) {
+        for (int k = tid; k < rows * kTile / 4; k += kThreads)
+            ((uint32_t*)sm.res)[k] = (((const uint32_t*)region)[k] & 0x07070707u) << kResFillShift;
+        return;
+    }
+    for (int k = tid; k < rows * 8; k += kThreads) {
+        const uint32_t word = ((const uint32_t*)region)[k];
+        uint32_t* r4 = (uint32_t*)(sm.res + (k >> 3) * kTile + 32 * (k & 7));
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint32_t b = word >> (4 * q);
+            r4[q] = ((b & 1u) ? kResFill : 0u) | ((b & 2u) ? kResFill << 8 : 0u) | ((b & 4u) ? kResFill << 16 : 0u) |
+                    ((b & 8u) ? kResFill << 24 : 0u);
         }
-        sm.res[k] = r;
     }
 }
 
@@ -1052,9 +1109,11 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
     const uint32_t n = p.n_dev ? min(*p.n_dev, p.n) : p.n;
     if (tile >= n) return;
     hv_tile_req q = p.reqs[tile];
-    bool ok = q.z <= 19 && q.x < (1u << q.z) && q.y < (1u << q.z) && q.r16 >= 1 && q.r16 <= 1024;
-    if constexpr (kKind == kPolyFill)
-        decode_outline(p, p.out + (uint64_t)tile * p.tile_bytes, sm, rows, strip, tid);
+    bool ok = q.z <= 19 && q.x < (1u << q.z) && q.y < (1u << q.z) && (p.R_units >= 0 || (q.r16 >= 1 && q.r16 <= 1024));
+    uint8_t* const region = p.out + (uint64_t)tile * p.tile_bytes + strip_offset(p.mode, rows, strip);
+    const bool aa_bytes = p.fill_aa && p.mode != HV_MODE_MASK;
+    if constexpr (kKind == HV_LAYER_POLYGONS)
+        decode_fill(region, sm, rows, tid, aa_bytes);
     else
         for (int k = tid; k < rows * kTile / 4; k += kThreads) ((uint32_t*)sm.res)[k] = 0u;
     if (!ok) {
@@ -1068,7 +1127,8 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
         const int32_t ps = 1 << (23 - z);
         const int32_t X0 = (int32_t)(-(int64_t)kGridHalf + (int64_t)q.x * ((int64_t)1 << (31 - z)));
         const int32_t Y0 = (int32_t)(-(int64_t)kGridHalf + (int64_t)q.y * ((int64_t)1 << (31 - z)));
-        const int32_t R = (int32_t)q.r16 << (19 - z);
+        // at most 2^29 either way (r16 <= 1024, or the buffer limit)
+        const int32_t R = p.R_units >= 0 ? p.R_units : (int32_t)q.r16 << (19 - z);
         const int32_t off = mask_mode ? 0 : (ps >> 2);
         // strip sample box
         const int32_t sx0 = X0 + (ps >> 1) - off, sx1 = X0 + (kTile - 1) * ps + (ps >> 1) + off;
@@ -1084,9 +1144,11 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
                            p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
         // Algorithm 2 over polygon boxes and edges
         if constexpr (kKind == kPolyFill) {
-            const int32_t cx0 = X0 + (ps >> 1), cx1 = X0 + (kTile - 1) * ps + (ps >> 1);
-            const int32_t cy0 = Y0 + strip * rows * ps + (ps >> 1);
-            const int32_t cy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1);
+            // the strip's centres, or its super-samples
+            const int32_t fo = aa_bytes ? (ps >> 2) : 0;
+            const int32_t cx0 = X0 + (ps >> 1) - fo, cx1 = X0 + (kTile - 1) * ps + (ps >> 1) + fo;
+            const int32_t cy0 = Y0 + strip * rows * ps + (ps >> 1) - fo;
+            const int32_t cy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1) + fo;
             stage<FillLeaf, kProf>(p, sm, p.mtree, p.mbr_obj, p.mbr_ids, p.mside, p.mside_obj, p.mside_ids,
                             learned ? &p.mlm : nullptr, p.mhalo, X0, Y0, strip, z, 0, mask_mode, cx0, cy0, cx1,
                             cy1, tid);
@@ -1095,13 +1157,31 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
     // ---- encode the strip (Sec. 4.1 Render Tiles) ----
     const long long t_enc = tick<kProf>();
     uint8_t* out = p.out + (uint64_t)tile * p.tile_bytes;
-    if (p.mode == HV_MODE_MASK) {
+    // global pixel coordinates of the strip's first pixel (fill patterns)
+    const uint32_t gx0 = q.x * (uint32_t)kTile, gy0 = q.y * (uint32_t)kTile + (uint32_t)(strip * rows);
+    if constexpr (kKind == kPolyFill) {
+        // the fill results for the outline part, in the strip's own region
+        if (aa_bytes) {
+            for (int k = tid; k < rows * kTile / 4; k += kThreads)
+                ((uint32_t*)region)[k] = (((const uint32_t*)sm.res)[k] >> kResFillShift) & 0x07070707u;
+        } else if (tid < rows * 8) {
+            const int jl = tid >> 3, w = tid & 7;
+            uint32_t word = 0;
+            for (int b = 0; b < 32; b++)
+                if (sm.res[jl * kTile + 32 * w + b] >> kResFillShift) word |= 1u << b;
+            ((uint32_t*)region)[tid] = word;
+        }
+    } else if (p.mode == HV_MODE_MASK) {
         // 16 rows x 8 words; word w of row j = pixels 32w .. 32w+31
         if (tid < rows * 8) {
             int jl = tid >> 3, w = tid & 7;
             uint32_t word = 0;
-            for (int b = 0; b < 32; b++)
-                if (sm.res[jl * kTile + 32 * w + b] & (kResCentre | kResFill)) word |= 1u << b;
+            for (int b = 0; b < 32; b++) {
+                const uint32_t f = sm.res[jl * kTile + 32 * w + b];
+                bool filled = (f >> kResFillShift) != 0;
+                if (filled && p.pat_w) filled = fill_texel(p, gx0 + 32 * w + b, gy0 + jl).w != 0;
+                if ((f & kResCentre) || filled) word |= 1u << b;
+            }
             ((uint32_t*)out)[(strip * rows + jl) * 8 + w] = word;
         }
     } else if (p.mode == HV_MODE_COVERAGE) {
@@ -1112,8 +1192,14 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
         for (int k = 0; k < 4; k++) {
             uint32_t v = 0;
             for (int b = 0; b < 4; b++) {
-                uint32_t f = r[4 * k + b];
-                uint32_t c = __popc(f & 15u) | ((f & kResFill) ? 8u : 0u);
+                const uint32_t f = r[4 * k + b];
+                uint32_t fill = f >> kResFillShift;
+                if (fill && p.pat_w) {
+                    const int px = tid * 16 + 4 * k + b;
+                    if (fill_texel(p, gx0 + (px & (kTile - 1)), gy0 + px / kTile).w == 0) fill = 0;
+                }
+                // anti-aliased: the fill count in bits 4-6; else bit 3 for a filled centre
+                const uint32_t c = __popc(f & 15u) | (p.fill_aa ? fill << 4 : (fill ? 8u : 0u));
                 v |= c << (8 * b);
             }
             w4[k] = v;
@@ -1130,12 +1216,29 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
                 uint32_t f = sm.res[px + b];
                 uint32_t v = __popc(f & 15u);
                 uint32_t a = (255u * v + 2u) >> 2;
+                // fill count: 0..4 anti-aliased, else 4 for a filled centre
+                uint32_t fc = f >> kResFillShift;
+                if (!p.fill_aa && fc) fc = 4;
+                uchar4 fill = p.fill;
+                if (fc && p.pat_w) {
+                    fill = fill_texel(p, gx0 + ((px + b) & (kTile - 1)), gy0 + (px + b) / kTile);
+                    if (fill.w == 0) fc = 0;   // a transparent texel: not filled
+                }
                 uint32_t rgba = 0;
-                if (f & kResFill) {
-                    uint32_t r = (p.line.x * a + p.fill.x * (255u - a) + 127u) / 255u;
-                    uint32_t g = (p.line.y * a + p.fill.y * (255u - a) + 127u) / 255u;
-                    uint32_t bl = (p.line.z * a + p.fill.z * (255u - a) + 127u) / 255u;
+                if (fc == 4) {
+                    uint32_t r = (p.line.x * a + fill.x * (255u - a) + 127u) / 255u;
+                    uint32_t g = (p.line.y * a + fill.y * (255u - a) + 127u) / 255u;
+                    uint32_t bl = (p.line.z * a + fill.z * (255u - a) + 127u) / 255u;
                     rgba = r | (g << 8) | (bl << 16) | (255u << 24);
+                } else if (fc) {
+                    // the outline over a partly covered fill
+                    const uint32_t af = (255u * fc + 2u) >> 2;
+                    const uint32_t A = (255u * a + af * (255u - a) + 127u) / 255u;
+                    const uint32_t den = 255u * A, wf = af * (255u - a), wl = a * 255u;
+                    const uint32_t r = (p.line.x * wl + fill.x * wf + 127u * A) / den;
+                    const uint32_t g = (p.line.y * wl + fill.y * wf + 127u * A) / den;
+                    const uint32_t bl = (p.line.z * wl + fill.z * wf + 127u * A) / den;
+                    rgba = r | (g << 8) | (bl << 16) | (A << 24);
                 } else if (v) {
                     rgba = (uint32_t)p.line.x | ((uint32_t)p.line.y << 8) | ((uint32_t)p.line.z << 16) | (a << 24);
                 }
@@ -1179,13 +1282,40 @@ LModel learned_model(const LearnedView& v);
 
 uint32_t render_launch_count(Layer* L, int) { return L->kind == HV_LAYER_POLYGONS ? 2u : 1u; }
 
+bool fill_style_ok(const hv_fill_style* f) {
+    if (!f) return true;
+    if (f->flags & ~(uint32_t)HV_FILL_AA) return false;
+    if (f->pattern_w == 0 && f->pattern_h == 0) return true;
+    if (f->pattern_w < 1 || f->pattern_h < 1 || f->pattern_w > kMaxPattern || f->pattern_h > kMaxPattern ||
+        !f->pattern_rgba)
+        return false;
+    for (uint32_t k = 0; k < f->pattern_w * f->pattern_h; k++)
+        if (f->pattern_rgba[4 * k + 3] != 0 && f->pattern_rgba[4 * k + 3] != 255) return false;
+    return true;
+}
+
 int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int index_kind,
                   const hv_style* style, uint8_t* d_out, cudaStream_t stream, const RenderLog* log,
-                  const uint32_t* n_dev) {
+                  const uint32_t* n_dev, int32_t R_units, const hv_fill_style* fill) {
     (void)index_kind;
     if (n == 0) return HV_OK;
     Params p;
     memset(&p, 0, sizeof(p));
+    p.R_units = R_units < 0 ? -1 : R_units;
+    if (fill && L->kind == HV_LAYER_POLYGONS) {
+        if (!fill_style_ok(fill)) {
+            set_error("invalid fill style (flags, pattern size 1..16, texel alpha 0 or 255)");
+            return HV_EINVAL;
+        }
+        p.fill_aa = (fill->flags & HV_FILL_AA) ? 1 : 0;
+        if (fill->pattern_w) {
+            p.pat_w = (int)fill->pattern_w;
+            p.pat_h = (int)fill->pattern_h;
+            for (uint32_t k = 0; k < fill->pattern_w * fill->pattern_h; k++)
+                p.pattern[k] = make_uchar4(fill->pattern_rgba[4 * k], fill->pattern_rgba[4 * k + 1],
+                                           fill->pattern_rgba[4 * k + 2], fill->pattern_rgba[4 * k + 3]);
+        }
+    }
     p.reqs = d_reqs;
     p.n = n;
     p.n_dev = n_dev;
@@ -1254,24 +1384,25 @@ int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int
     }
     if (prof) {
         // the instrumented instantiations (phase profile); polygon layers
-        // profile their two launches into two halves of the counters
+        // profile their two launches (fill, outline) into two sets of counters
         if (L->kind == HV_LAYER_POINTS)
             k_render<HV_LAYER_POINTS, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
         else if (L->kind == HV_LAYER_LINES)
             k_render<HV_LAYER_LINES, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
         else {
-            k_render<HV_LAYER_POLYGONS, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+            k_render<kPolyFill, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
             Params q = p;
             q.phases = p.phases + kPN;
-            k_render<kPolyFill, true><<<(unsigned)grid, kThreads, 0, stream>>>(q);
+            k_render<HV_LAYER_POLYGONS, true><<<(unsigned)grid, kThreads, 0, stream>>>(q);
         }
     } else if (L->kind == HV_LAYER_POINTS)
         k_render<HV_LAYER_POINTS, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
     else if (L->kind == HV_LAYER_LINES)
         k_render<HV_LAYER_LINES, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
     else {
-        k_render<HV_LAYER_POLYGONS, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        // the fill first: the outline reads its bits and writes the tile
         k_render<kPolyFill, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        k_render<HV_LAYER_POLYGONS, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
     }
     HV_CUDA(cudaGetLastError());
     return HV_OK;

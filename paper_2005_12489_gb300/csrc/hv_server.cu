@@ -13,10 +13,15 @@
 // slot, so their work overlaps on the device (continuous batching).  Results
 // are handed out zero-copy from the slot's pinned buffer; a slot is recycled
 // after the poll that follows the one that exported its last result.
+// At submission (Parse Tasks), a request whose tile the layer cannot reach is
+// completed at once with an all-zero tile, and, with a result pool, one whose
+// tile is in the pool is completed from it; the worker stores every rendered
+// tile in the pool.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <thread>
 #include <vector>
 
@@ -62,7 +67,8 @@ struct Done {
     uint32_t bytes;
     const uint8_t* data;
     double t_submit, t_start, t_done;
-    int slot;
+    int slot;                                      // -1: completed at submission
+    std::shared_ptr<std::vector<uint8_t>> own;     // a tile from the result pool
 };
 
 }  // namespace
@@ -82,6 +88,10 @@ struct Server {
     uint64_t queued = 0, seq = 0;
     std::deque<Done> done;
     std::vector<int> exported;     // slots whose results the last poll handed out
+    std::vector<std::shared_ptr<std::vector<uint8_t>>> held;   // pool tiles the last poll handed out
+    std::vector<uint8_t> zeros;    // the all-zero tile of unreachable requests
+    ResultPool* pool = nullptr;
+    uint64_t pool_hits = 0, empty_tiles = 0;
     std::thread worker;
     bool stopping = false;
     bool failed = false;
@@ -145,12 +155,27 @@ int launch_batch(Server* S, int k) {
     return HV_OK;
 }
 
+// Can no object of the layer reach the tile?  Every sample lies inside the
+// tile, so an object within R of one meets the tile's box widened by R, and
+// a filled centre lies inside a polygon's box: both within the box of all the
+// layer's objects (the R-tree's root box).
+bool tile_unreachable(const Layer* L, const hv_tile_req& q) {
+    const TreeView& v = L->tree.view;
+    if (v.top == 0) return true;
+    const int64_t span = (int64_t)1 << (31 - q.z);
+    const int64_t X0 = -(int64_t)kGridHalf + (int64_t)q.x * span, Y0 = -(int64_t)kGridHalf + (int64_t)q.y * span;
+    const int64_t R = (int64_t)q.r16 << (19 - q.z);
+    const int4 b = v.root_box;
+    return b.x > X0 + span + R || b.z < X0 - R || b.y > Y0 + span + R || b.w < Y0 - R;
+}
+
 void worker_main(Server* S) {
     cudaSetDevice(S->ctx->device);
-    std::vector<int> to_launch;
+    std::vector<int> to_launch, to_pool;
     while (true) {
         bool busy = false;
         to_launch.clear();
+        to_pool.clear();
         {
             std::unique_lock<std::mutex> g(S->mu);
             // retire finished batches into the result pool
@@ -164,9 +189,11 @@ void worker_main(Server* S) {
                 if (e != cudaSuccess) { S->error = cudaGetErrorString(e); cudaGetLastError(); }
                 uint64_t tb = hv_tile_bytes(sl.items[0].req.mode);
                 for (auto& it : sl.items)
-                    S->done.push_back({it.tag, st, (uint32_t)tb, sl.h_out + it.offset, it.t_submit, sl.t_start, t, (int)k});
+                    S->done.push_back({it.tag, st, (uint32_t)tb, sl.h_out + it.offset, it.t_submit, sl.t_start, t,
+                                       (int)k, nullptr});
                 sl.outstanding = (int)sl.items.size();
                 sl.state = 2;
+                if (S->pool && st == HV_OK) to_pool.push_back((int)k);
             }
             // form batches for free slots: the oldest request's group, FIFO
             // within the group, while tile count and slot memory allow
@@ -190,11 +217,18 @@ void worker_main(Server* S) {
                 sl.t_start = now_us();
                 to_launch.push_back((int)k);
             }
-            if (S->stopping && S->queued == 0 && !busy && to_launch.empty()) break;
-            if (!busy && to_launch.empty()) {
+            if (S->stopping && S->queued == 0 && !busy && to_launch.empty() && to_pool.empty()) break;
+            if (!busy && to_launch.empty() && to_pool.empty()) {
                 S->cv.wait_for(g, std::chrono::microseconds(200));
                 continue;
             }
+        }
+        // store the retired tiles in the result pool (only this thread
+        // launches into a slot, so its tiles stay put meanwhile)
+        for (int k : to_pool) {
+            const Slot& sl = S->slots[k];
+            const uint64_t tb = hv_tile_bytes(sl.items[0].req.mode);
+            for (const auto& it : sl.items) pool_insert(S->pool, it.req, &S->opts.style, sl.h_out + it.offset, tb);
         }
         for (int k : to_launch) {
             int rc = launch_batch(S, k);
@@ -252,6 +286,8 @@ int hv_server_start(hv_ctx* ctx, hv_layer* const* layers, uint32_t n_layers, con
         }
         S->layers.push_back(L);
     }
+    S->pool = (ResultPool*)S->opts.pool;
+    S->zeros.assign(hv_tile_bytes(HV_MODE_RGBA), 0);
     S->max_batch = S->opts.max_batch ? S->opts.max_batch : 64;
     if (S->max_batch > 4096) S->max_batch = 4096;
     if (!S->opts.queue_capacity) S->opts.queue_capacity = 65536;
@@ -294,10 +330,27 @@ int hv_server_submit(hv_server* srv, const hv_tile_req* req, uint64_t tag) {
         set_error("hv_server_submit: request out of range");
         return HV_ERANGE;
     }
+    const double t = now_us();
+    const uint32_t tb = (uint32_t)hv_tile_bytes(q.mode);
+    // Parse Tasks: tiles the layer cannot reach, and tiles already in the pool
+    std::shared_ptr<std::vector<uint8_t>> hit;
+    const bool empty = tile_unreachable(S->layers[q.layer], q);
+    if (!empty && S->pool) {
+        auto v = std::make_shared<std::vector<uint8_t>>();
+        if (pool_lookup(S->pool, q, &S->opts.style, v.get()) && v->size() == tb) hit = v;
+    }
     std::lock_guard<std::mutex> g(S->mu);
     if (S->stopping) { set_error("hv_server_submit: server is stopping"); return HV_ESTATE; }
+    if (empty || hit) {
+        S->done.push_back({tag, HV_OK, tb, hit ? hit->data() : S->zeros.data(), t, t, t, -1, hit});
+        if (hit)
+            S->pool_hits++;
+        else
+            S->empty_tiles++;
+        return HV_OK;
+    }
     if (S->queued >= S->opts.queue_capacity) { set_error("hv_server_submit: queue full"); return HV_EBUSY; }
-    S->queues[((uint32_t)q.layer << 8) | q.mode].push_back({q, tag, now_us(), S->seq++, 0});
+    S->queues[((uint32_t)q.layer << 8) | q.mode].push_back({q, tag, t, S->seq++, 0});
     S->queued++;
     S->cv.notify_one();
     return HV_OK;
@@ -313,6 +366,7 @@ int hv_server_poll(hv_server* srv, hv_done* out, uint32_t max, uint32_t* n_out) 
         if (sl.state == 3 && sl.outstanding == 0) sl.state = 0;
     }
     S->exported.clear();
+    S->held.clear();
     uint32_t n = 0;
     while (n < max && !S->done.empty()) {
         Done d = S->done.front();
@@ -324,10 +378,14 @@ int hv_server_poll(hv_server* srv, hv_done* out, uint32_t max, uint32_t* n_out) 
         out[n].t_submit_us = d.t_submit;
         out[n].t_start_us = d.t_start;
         out[n].t_done_us = d.t_done;
-        Slot& sl = S->slots[d.slot];
-        if (--sl.outstanding == 0) {
-            sl.state = 3;
-            S->exported.push_back(d.slot);
+        if (d.slot >= 0) {
+            Slot& sl = S->slots[d.slot];
+            if (--sl.outstanding == 0) {
+                sl.state = 3;
+                S->exported.push_back(d.slot);
+            }
+        } else if (d.own) {
+            S->held.push_back(d.own);
         }
         n++;
     }
@@ -375,9 +433,13 @@ int hv_server_stop(hv_server* srv) {
 
 // Open-loop replay: submit reqs[i] at arrival_us[i] (relative to the call)
 // from this thread, poll completions, and record each request's latency
-// (done - arrival, microseconds) into latency_us[i] (tags are indices).
-int hv_server_replay(hv_server* srv, const hv_tile_req* reqs, const double* arrival_us, uint64_t n,
-                     double* latency_us, double* wall_us) {
+// (done - arrival, microseconds) into latency_us[i] (tags are indices) and,
+// if parts_us is given, its parts: parts_us[4i..4i+3] = wait before
+// submission (the queue was full), task-pool wait (submission -> batch
+// launch), service (launch -> completion seen by the worker: copies and
+// kernels), hand-out (completion -> this thread's poll).
+int hv_server_replay_detail(hv_server* srv, const hv_tile_req* reqs, const double* arrival_us, uint64_t n,
+                            double* latency_us, double* parts_us, double* wall_us) {
     if (!srv || (n && (!reqs || !arrival_us || !latency_us)) || !wall_us) {
         set_error("hv_server_replay: NULL argument");
         return HV_EINVAL;
@@ -404,12 +466,34 @@ int hv_server_replay(hv_server* srv, const hv_tile_req* reqs, const double* arri
                           buf[i].status, S->error.c_str());
                 return buf[i].status;
             }
-            latency_us[buf[i].tag] = buf[i].t_done_us - submit_at[buf[i].tag];
+            const uint64_t k = buf[i].tag;
+            const double polled = now_us();
+            latency_us[k] = buf[i].t_done_us - submit_at[k];
+            if (parts_us) {
+                parts_us[4 * k] = buf[i].t_submit_us - submit_at[k];
+                parts_us[4 * k + 1] = buf[i].t_start_us - buf[i].t_submit_us;
+                parts_us[4 * k + 2] = buf[i].t_done_us - buf[i].t_start_us;
+                parts_us[4 * k + 3] = polled - buf[i].t_done_us;
+            }
             finished++;
         }
         if (got == 0) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     *wall_us = now_us() - t0;
+    return HV_OK;
+}
+
+int hv_server_replay(hv_server* srv, const hv_tile_req* reqs, const double* arrival_us, uint64_t n,
+                     double* latency_us, double* wall_us) {
+    return hv_server_replay_detail(srv, reqs, arrival_us, n, latency_us, nullptr, wall_us);
+}
+
+int hv_server_shortcuts(hv_server* srv, uint64_t* pool_hits, uint64_t* empty_tiles) {
+    if (!srv) return HV_EINVAL;
+    Server* S = (Server*)srv;
+    std::lock_guard<std::mutex> g(S->mu);
+    if (pool_hits) *pool_hits = S->pool_hits;
+    if (empty_tiles) *empty_tiles = S->empty_tiles;
     return HV_OK;
 }
 

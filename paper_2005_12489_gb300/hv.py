@@ -23,7 +23,10 @@ STATUS_NAMES = ["HV_OK", "HV_EINVAL", "HV_ERANGE", "HV_ENOMEM", "HV_ECUDA", "HV_
 HV_MODE_MASK, HV_MODE_COVERAGE, HV_MODE_RGBA = 0, 1, 2
 HV_LAYER_POINTS, HV_LAYER_LINES, HV_LAYER_POLYGONS = 0, 1, 2
 HV_INDEX_RTREE, HV_INDEX_LEARNED = 1, 2
+HV_OVERLAY_AND, HV_OVERLAY_OR, HV_OVERLAY_XOR, HV_OVERLAY_DIFF = 0, 1, 2, 3
+HV_FILL_AA = 1
 HV_LEARNED_NO_MLP = 0xFFFFFFFF     # hv_build_opts.learned_hidden: linear pieces only
+HV_PLACE_DEVICE, HV_PLACE_HOST = 0, 1
 
 REQ_DTYPE = np.dtype([("x", "<u4"), ("y", "<u4"), ("r16", "<u2"), ("z", "u1"), ("mode", "u1"),
                       ("layer", "<u4")])
@@ -40,10 +43,16 @@ class hv_style(ctypes.Structure):
     _fields_ = [("line_rgba", ctypes.c_uint8 * 4), ("fill_rgba", ctypes.c_uint8 * 4)]
 
 
+class hv_fill_style(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("pattern_w", ctypes.c_uint32), ("pattern_h", ctypes.c_uint32),
+                ("pattern_rgba", ctypes.c_void_p)]
+
+
 class hv_build_opts(ctypes.Structure):
     _fields_ = [("learned_segments", ctypes.c_uint32), ("learned_hidden", ctypes.c_uint32),
                 ("learned_steps", ctypes.c_uint32), ("learned_seed", ctypes.c_uint32),
-                ("max_error", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("max_error", ctypes.c_uint32), ("object_placement", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class hv_layer_info(ctypes.Structure):
@@ -57,13 +66,19 @@ class hv_layer_info(ctypes.Structure):
                 ("learned_mean_error", ctypes.c_double), ("learned_pieces", ctypes.c_uint32),
                 ("learned_mlp", ctypes.c_uint32), ("learned_halo", ctypes.c_int32),
                 ("piece_extent", ctypes.c_int32), ("index_records", ctypes.c_uint64),
-                ("learned_mean_window", ctypes.c_double), ("learned_mean_window_linear", ctypes.c_double)]
+                ("learned_mean_window", ctypes.c_double), ("learned_mean_window_linear", ctypes.c_double),
+                ("host_bytes", ctypes.c_uint64)]
 
 
 class hv_server_opts(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_uint32), ("queue_capacity", ctypes.c_uint32),
                 ("scratch_bytes", ctypes.c_uint64), ("index_kind", ctypes.c_uint32),
-                ("use_graphs", ctypes.c_uint32), ("style", hv_style)]
+                ("use_graphs", ctypes.c_uint32), ("style", hv_style), ("pool", ctypes.c_void_p)]
+
+
+class hv_pool_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("hits", "misses", "inserts", "evictions", "expirations",
+                                                "rejected", "entries", "bytes", "capacity")]
 
 
 class hv_done(ctypes.Structure):
@@ -80,6 +95,8 @@ I32 = ctypes.c_int
 
 SIGNATURES = {
     "hv_create": [ctypes.POINTER(P), I32, U64],
+    "hv_lonlat_to_grid": [P, U64, P],
+    "hv_route_tiles": [P, U64, U32, P],
     "hv_destroy": [P],
     "hv_last_error": [],
     "hv_ctx_device_bytes": [P, ctypes.POINTER(U64)],
@@ -100,12 +117,23 @@ SIGNATURES = {
     "hv_render_tiles_counted": [P, P, U32, I32, I32, P, P, U64, P, U64, P, P],
     "hv_render_tiles_phases": [P, P, U32, I32, I32, P, P, U64, P, P],
     "hv_render_launches": [P, I32, ctypes.POINTER(U32)],
+    "hv_render_buffer": [P, P, U32, I32, I32, ctypes.c_int32, P, P, U64, P],
+    "hv_render_tiles_styled": [P, P, U32, I32, I32, P, P, P, U64, P],
+    "hv_overlay_tiles": [P, ctypes.c_int32, P, ctypes.c_int32, I32, P, U32, I32, P, U64, P],
     "hv_server_start": [P, P, U32, ctypes.POINTER(hv_server_opts), ctypes.POINTER(P)],
     "hv_server_submit": [P, P, U64],
     "hv_server_poll": [P, ctypes.POINTER(hv_done), U32, ctypes.POINTER(U32)],
     "hv_server_stop": [P],
     "hv_server_replay": [P, P, P, U64, P, ctypes.POINTER(ctypes.c_double)],
+    "hv_server_replay_detail": [P, P, P, U64, P, P, ctypes.POINTER(ctypes.c_double)],
     "hv_server_stats": [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U32)],
+    "hv_server_shortcuts": [P, ctypes.POINTER(U64), ctypes.POINTER(U64)],
+    "hv_result_pool_create": [U64, U32, ctypes.POINTER(P)],
+    "hv_result_pool_destroy": [P],
+    "hv_result_pool_put": [P, P, P, P, U64],
+    "hv_result_pool_get": [P, P, P, P, U64, ctypes.POINTER(U32)],
+    "hv_result_pool_stats": [P, ctypes.POINTER(hv_pool_stats)],
+    "hv_result_pool_clear": [P],
 }
 
 
@@ -161,6 +189,23 @@ def hv_last_error():
 
 def hv_tile_bytes(mode):
     return int(lib().hv_tile_bytes(mode))
+
+
+def hv_lonlat_to_grid(lonlat):
+    """(n, 2) degrees (lon, lat) -> (n, 2) int32 grid coordinates."""
+    a = np.ascontiguousarray(np.asarray(lonlat, dtype=np.float64).reshape(-1, 2))
+    out = np.zeros(a.shape, dtype=np.int32)
+    _check(lib().hv_lonlat_to_grid(ptr(a), a.shape[0], ptr(out)))
+    return out
+
+
+def hv_route_tiles(reqs, n_ranks):
+    """Rank (0..n_ranks-1) of every request: a hash of its (layer, z, x, y)."""
+    r = reqs if isinstance(reqs, np.ndarray) and reqs.dtype == REQ_DTYPE else make_requests(reqs)
+    r = np.ascontiguousarray(r)
+    out = np.zeros(len(r), dtype=np.uint32)
+    _check(lib().hv_route_tiles(ptr(r), len(r), n_ranks, ptr(out)))
+    return out
 
 
 def hv_create(device=0, mem_budget=0):
@@ -309,6 +354,39 @@ def hv_render_tiles_static(layer, reqs, n, mode, index_kind, style, out, out_byt
                                         out_bytes, stream_handle(stream)))
 
 
+def make_fill_style(aa=False, pattern=None):
+    """A fill style: anti-aliased fill and / or a (h, w, 4) uint8 RGBA pattern.
+    The returned structure keeps the pattern array alive."""
+    f = hv_fill_style()
+    f.flags = HV_FILL_AA if aa else 0
+    if pattern is not None:
+        pat = np.ascontiguousarray(np.asarray(pattern, dtype=np.uint8))
+        f.pattern_h, f.pattern_w = pat.shape[:2]
+        f.pattern_rgba = pat.ctypes.data
+        f._pattern = pat
+    return f
+
+
+def hv_render_tiles_styled(layer, reqs, n, mode, index_kind, style, fill, out, out_bytes, stream=None):
+    _check(lib().hv_render_tiles_styled(layer, ptr(reqs), n, mode, index_kind,
+                                        ctypes.byref(style) if style is not None else None,
+                                        ctypes.byref(fill) if fill is not None else None, ptr(out), out_bytes,
+                                        stream_handle(stream)))
+
+
+def hv_render_buffer(layer, reqs, n, mode, index_kind, radius_units, style, out, out_bytes, stream=None):
+    """hv_render_tiles with one radius in grid units for every tile."""
+    _check(lib().hv_render_buffer(layer, ptr(reqs), n, mode, index_kind, radius_units,
+                                  ctypes.byref(style) if style is not None else None, ptr(out), out_bytes,
+                                  stream_handle(stream)))
+
+
+def hv_overlay_tiles(layer_a, radius_a, layer_b, radius_b, op, reqs, n, index_kind, out, out_bytes, stream=None):
+    """MASK tiles of op(buffer of layer_a at radius_a, buffer of layer_b at radius_b)."""
+    _check(lib().hv_overlay_tiles(layer_a, radius_a, layer_b, radius_b, op, ptr(reqs), n, index_kind, ptr(out),
+                                  out_bytes, stream_handle(stream)))
+
+
 def hv_layer_take_status(layer, stream=None):
     out = U32()
     _check(lib().hv_layer_take_status(layer, stream_handle(stream), ctypes.byref(out)))
@@ -355,20 +433,76 @@ def hv_server_replay(srv, reqs, arrival_us):
     return lat, wall.value
 
 
+def hv_server_replay_detail(srv, reqs, arrival_us):
+    """Open-loop replay; returns (latency_us, parts_us (n, 4): pre-submit wait,
+    task-pool wait, service, hand-out), wall_us)."""
+    arr = np.ascontiguousarray(arrival_us, dtype=np.float64)
+    lat = np.zeros(len(reqs), dtype=np.float64)
+    parts = np.zeros((len(reqs), 4), dtype=np.float64)
+    wall = ctypes.c_double()
+    _check(lib().hv_server_replay_detail(srv, ptr(reqs), ptr(arr), len(reqs), ptr(lat), ptr(parts),
+                                         ctypes.byref(wall)))
+    return lat, parts, wall.value
+
+
 def hv_server_stats(srv):
     b, t, g, s = U64(), U64(), U64(), U32()
     _check(lib().hv_server_stats(srv, ctypes.byref(b), ctypes.byref(t), ctypes.byref(g), ctypes.byref(s)))
     return {"batches": b.value, "tiles": t.value, "graph_launches": g.value, "slots": s.value}
 
 
+def hv_server_shortcuts(srv):
+    h, e = U64(), U64()
+    _check(lib().hv_server_shortcuts(srv, ctypes.byref(h), ctypes.byref(e)))
+    return {"pool_hits": h.value, "empty_tiles": e.value}
+
+
 def make_server_opts(max_batch=64, queue_capacity=0, scratch_bytes=0, index_kind=HV_INDEX_RTREE,
-                     use_graphs=1, style=None):
+                     use_graphs=1, style=None, pool=None):
     o = hv_server_opts()
     o.max_batch, o.queue_capacity, o.scratch_bytes = max_batch, queue_capacity, scratch_bytes
     o.index_kind, o.use_graphs = index_kind, use_graphs
     if style is not None:
         o.style = style
+    o.pool = pool
     return o
+
+
+# ---- result pool ---------------------------------------------------------------
+
+def hv_result_pool_create(capacity_bytes, ttl_ms=0):
+    out = P()
+    _check(lib().hv_result_pool_create(capacity_bytes, ttl_ms, ctypes.byref(out)))
+    return out.value
+
+
+def hv_result_pool_destroy(pool):
+    _check(lib().hv_result_pool_destroy(pool))
+
+
+def hv_result_pool_put(pool, req, style, data, nbytes=None):
+    """req: one hv_tile_req record (numpy REQ_DTYPE); data: host bytes."""
+    n = data.nbytes if nbytes is None else nbytes
+    _check(lib().hv_result_pool_put(pool, ptr(req), ctypes.byref(style) if style is not None else None,
+                                    ptr(data), n))
+
+
+def hv_result_pool_get(pool, req, style, out):
+    """Returns True on a hit (the tile is copied into `out`)."""
+    hit = U32()
+    _check(lib().hv_result_pool_get(pool, ptr(req), ctypes.byref(style) if style is not None else None,
+                                    ptr(out), out.nbytes, ctypes.byref(hit)))
+    return bool(hit.value)
+
+
+def hv_result_pool_stats(pool):
+    st = hv_pool_stats()
+    _check(lib().hv_result_pool_stats(pool, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in st._fields_}
+
+
+def hv_result_pool_clear(pool):
+    _check(lib().hv_result_pool_clear(pool))
 
 
 # ---- convenience: render host arrays into a numpy result --------------------

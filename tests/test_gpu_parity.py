@@ -402,6 +402,35 @@ def test_host_output_in_chunks(ctx):
         hv.hv_layer_free(L)
 
 
+@pytest.mark.parametrize("kind", ["points", "polygons"])
+def test_pinned_host_output_written_by_the_kernels(ctx, kind):
+    """Pinned host output is written by the kernels over the CPU-GPU link
+    (the polygon layers' fill bits read back from it too): equal to the
+    oracle in every mode, with host and with device requests."""
+    if kind == "points":
+        pts = gen.gmm_points(100_000, seed=25, k=8)
+        L = points_layer(ctx, pts)
+        reqs = gen.density_tiles(pts, 300, 4, 14, [8, 32], seed=26)
+        ref = lambda m: oracle.render_points(pts, reqs, m, STYLE_T)
+    else:
+        xy, ro, po = gen.star_polygons(2_000, seed=27, k=8, rho_median=6e-4)
+        L = hv.hv_layer_load_polygons(ctx, xy, ro, po)
+        hv.hv_layer_build_index(L)
+        reqs = gen.density_tiles(gen.polygon_centres(xy, ro, po), 40, 3, 12, 8, seed=28)
+        ref = lambda m: oracle.render_polygons(xy, ro, po, reqs, m, STYLE_T)
+    try:
+        d_req = torch.from_numpy(hv.make_requests(reqs).view(np.uint8).copy()).cuda()
+        for mode in MODES:
+            want = ref(mode)
+            for rq in (hv.make_requests(reqs), d_req):
+                out = torch.full((len(reqs), hv.hv_tile_bytes(mode)), 0xAB, dtype=torch.uint8, pin_memory=True)
+                hv.hv_render_tiles(L, rq, len(reqs), mode, hv.HV_INDEX_RTREE, style(), out, out.numel(),
+                                   torch.cuda.current_stream())
+                assert np.array_equal(out.numpy(), want)
+    finally:
+        hv.hv_layer_free(L)
+
+
 @pytest.mark.parametrize("kind", ["points", "lines", "polygons"])
 def test_phase_profile_launch(ctx, kind):
     """The instrumented (phase-profile) launch renders the oracle's tiles, and

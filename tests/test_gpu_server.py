@@ -175,10 +175,61 @@ def test_open_loop_replay(ctx, layers):
     arrival = np.cumsum(np.random.default_rng(61).exponential(1e6 / 20000.0, size=len(reqs)))
     srv = hv.hv_server_start(ctx, Ls, hv.make_server_opts(max_batch=32, scratch_bytes=1 << 30))
     try:
-        lat, wall = hv.hv_server_replay(srv, reqs, arrival)
+        lat, parts, wall = hv.hv_server_replay_detail(srv, reqs, arrival)
         stats = hv.hv_server_stats(srv)
+        short = hv.hv_server_shortcuts(srv)
     finally:
         hv.hv_server_stop(srv)
     assert (lat > 0).all() and np.isfinite(lat).all()
     assert wall >= arrival[-1]
-    assert stats["tiles"] == len(reqs) and stats["batches"] <= len(reqs)
+    # the first three parts of each latency add up to it (clock reads apart);
+    # the fourth is the time until the replay polled the result
+    assert (parts >= -1.0).all() and np.allclose(parts[:, :3].sum(1), lat, atol=5.0)
+    # tiles no object reaches complete at submission, without a launch
+    assert stats["tiles"] + short["empty_tiles"] == len(reqs)
+    assert stats["batches"] <= len(reqs)
+
+
+def test_result_pool_and_unreachable_tiles(ctx, layers):
+    """Parse Tasks (Sec. 4.1) drops tiles already in the Result Pool (Sec. 4.2)
+    and tiles outside the data: requests served a second time come from the
+    pool, under a capacity that forces evictions, and tiles no object can
+    reach complete at submission as zeros; every tile equals the oracle's."""
+    Ls, anchors, src = layers
+    style = hv.make_style(*STYLE)
+    reqs = mixed_requests(anchors, 90, seed=91)
+    # room for about half of the tiles: the first round evicts, and the
+    # second, submitted at once, finds the later half
+    total = sum(hv.hv_tile_bytes(int(m)) for m in reqs["mode"])
+    pool = hv.hv_result_pool_create(total // 2)
+    srv = hv.hv_server_start(ctx, Ls, hv.make_server_opts(max_batch=8, scratch_bytes=8 * 262144 * 4,
+                                                          style=style, pool=pool))
+    try:
+        ref = oracle_tiles(src, reqs)
+        for rnd in range(2):
+            for i in range(len(reqs)):
+                assert hv.hv_server_submit(srv, reqs[i:i + 1], 100 * rnd + i) == hv.HV_OK
+            got = poll_all(srv, len(reqs))
+            for i in range(len(reqs)):
+                assert got[100 * rnd + i] == ref[i], "round %d request %d" % (rnd, i)
+        sc = hv.hv_server_shortcuts(srv)
+        st = hv.hv_result_pool_stats(pool)
+        assert sc["pool_hits"] > 0 and st["hits"] == sc["pool_hits"]
+        assert st["inserts"] >= len(reqs) and st["evictions"] > 0 and st["bytes"] <= st["capacity"]
+        # tiles of the polygon layer far from all of its polygons
+        far = np.zeros(6, dtype=hv.REQ_DTYPE)
+        far["z"], far["x"], far["y"] = 19, [0, 1, 5, (1 << 19) - 1, 0, 7], [0, 0, 9, (1 << 19) - 1, 3, 0]
+        far["r16"], far["layer"], far["mode"] = 48, 2, [0, 1, 2, 2, 1, 0]
+        before = sc["empty_tiles"]
+        launched = hv.hv_server_stats(srv)["tiles"]
+        for i in range(len(far)):
+            assert hv.hv_server_submit(srv, far[i:i + 1], 1000 + i) == hv.HV_OK
+        got = poll_all(srv, len(far))
+        fref = oracle_tiles(src, far)
+        for i in range(len(far)):
+            assert got[1000 + i] == fref[i] and not any(got[1000 + i])
+        assert hv.hv_server_shortcuts(srv)["empty_tiles"] == before + len(far)
+        assert hv.hv_server_stats(srv)["tiles"] == launched          # no GPU work for them
+    finally:
+        hv.hv_server_stop(srv)
+        hv.hv_result_pool_destroy(pool)
