@@ -440,7 +440,8 @@ def phase_profile(hv, torch, layer, d_req, n, mode, index, style, d_out, kind):
                       "frontier_scan": (busy - desc) / tot, "node_tests": (desc - leaf) / tot,
                       "leaf_visits": leaf / tot, "blocks_waiting": (c[4] - busy) / tot, "encode": c[8] / tot},
             "per_tile": {"blocks": c[10] / n, "leaf_visits": c[11] / n, "node_visits": c[12] / n,
-                         "frontier_tests": c[13] / n},
+                         "frontier_tests": c[13] / n, "leaf_visits_empty": c[14] / n,
+                         "leaf_visits_deciding": c[15] / n},
             "warp_cycles_per_tile": tot / n}
     return parts
 

@@ -114,6 +114,8 @@ typedef struct hv_style {
  * (256 x + i, 256 y + j) of tile (z, x, y) takes texel
  * ((256 y + j) mod pattern_h, (256 x + i) mod pattern_w); a transparent
  * texel leaves the pixel unfilled, an opaque one gives the fill colour.
+ * The texels go to a small stream-ordered device copy for the call
+ * (cudaMallocAsync / cudaFreeAsync on `stream`).
  * RGBA with fill count f and outline count v: a = (255 v + 2) >> 2,
  * a_f = (255 f + 2) >> 2, A = (255 a + a_f (255 - a) + 127) / 255, each
  * channel (line a 255 + fill a_f (255 - a) + 127 A) / (255 A); for f = 4 this
@@ -363,7 +365,10 @@ enum {
     HV_PHASE_BLOCK_COUNT,     /*   8 x 4 pixel blocks, */
     HV_PHASE_LEAF_VISITS,     /*   leaf visits, */
     HV_PHASE_NODE_VISITS,     /*   inner-node visits in descents, */
-    HV_PHASE_FRONTIER_TESTS,  /*   frontier entries tested by blocks */
+    HV_PHASE_FRONTIER_TESTS,  /*   frontier entries tested by blocks, */
+    HV_PHASE_LEAF_EMPTY,      /*   leaf visits with no record in reach of an
+                                   undecided sample, */
+    HV_PHASE_LEAF_DECIDED,    /*   leaf visits that decided a sample */
     HV_PHASE_COUNT = 16
 };
 

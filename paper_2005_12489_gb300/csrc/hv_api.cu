@@ -516,8 +516,24 @@ static int render_impl(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int
             }
         }
     }
+    // a fill pattern's texels go to a stream-ordered device copy, freed in
+    // stream order after the launches that read it
+    void* pattern_dev = nullptr;
+    if (fill && fill->pattern_w && L->kind == HV_LAYER_POLYGONS) {
+        const uint64_t pb = (uint64_t)fill->pattern_w * fill->pattern_h * 4;
+        HV_CUDA(cudaMallocAsync(&pattern_dev, pb, st));
+        HV_CUDA(cudaMemcpyAsync(pattern_dev, fill->pattern_rgba, pb, cudaMemcpyHostToDevice, st));
+    }
+    struct PatternRelease {
+        void* p;
+        cudaStream_t st;
+        ~PatternRelease() {
+            if (p) cudaFreeAsync(p, st);
+        }
+    } release{pattern_dev, st};
     if (dev_reqs && dev_out)
-        return launch_render(L, reqs, n, mode, index_kind, style, (uint8_t*)out, st, nullptr, nullptr, R_units, fill);
+        return launch_render(L, reqs, n, mode, index_kind, style, (uint8_t*)out, st, nullptr, nullptr, R_units, fill,
+                             pattern_dev);
     std::lock_guard<std::mutex> g(c->render_mu);
     const hv_tile_req* d_reqs = reqs;
     if (!dev_reqs) {
@@ -528,7 +544,7 @@ static int render_impl(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int
     }
     if (dev_out || pinned_out) {
         HV_TRY(launch_render(L, d_reqs, n, mode, index_kind, style, (uint8_t*)(dev_out ? out : pinned_out), st,
-                             nullptr, nullptr, R_units, fill));
+                             nullptr, nullptr, R_units, fill, pattern_dev));
         // the request staging must be consumed before the next call reuses
         // it, and host output must be complete when the call returns
         HV_CUDA(cudaStreamSynchronize(st));
@@ -552,7 +568,7 @@ static int render_impl(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int
         int b = i & 1;
         HV_CUDA(cudaStreamWaitEvent(st, c->ev_copied[b], 0));   // buffer free
         HV_TRY(launch_render(L, d_reqs + first, cnt, mode, index_kind, style, bufs[b], st, nullptr, nullptr,
-                             R_units, fill));
+                             R_units, fill, pattern_dev));
         HV_CUDA(cudaEventRecord(c->ev_rendered[b], st));
         return HV_OK;
     };

@@ -175,7 +175,7 @@ struct RenderLog {
 int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int index_kind,
                   const hv_style* style, uint8_t* d_out, cudaStream_t stream,
                   const RenderLog* log = nullptr, const uint32_t* n_dev = nullptr, int32_t R_units = -1,
-                  const hv_fill_style* fill = nullptr);
+                  const hv_fill_style* fill = nullptr, const void* pattern_dev = nullptr);
 // A fill style is valid: HV_FILL_AA or 0, and a pattern of at most 16 x 16
 // texels with alpha 0 or 255 (or none).
 bool fill_style_ok(const hv_fill_style* fill);

@@ -87,7 +87,7 @@ struct Params {
     // RGBA texels (0: none) laid over the global pixel grid
     int fill_aa;
     int pat_w, pat_h;
-    uchar4 pattern[kMaxPattern * kMaxPattern];
+    const uchar4* pattern;      // device memory, pat_w * pat_h texels
     LModel lm, mlm;
     int32_t halo, mhalo;
     TreeArg side, mside;
@@ -111,7 +111,7 @@ struct Params {
 // cycles.  The indices are the HV_PHASE_* values of the C header.
 enum {
     kPTotal = 0, kPPrologue, kPCull, kPBin, kPBlocksCta, kPBlocksWarp, kPLeaf, kPDescend, kPEncode,
-    kPCtas, kPBlocks, kPLeafVisits, kPNodeVisits, kPFrontierEntries, kPN = 16
+    kPCtas, kPBlocks, kPLeafVisits, kPNodeVisits, kPFrontierEntries, kPLeafEmpty, kPLeafDecided, kPN = 16
 };
 
 template <bool kProf>
@@ -119,6 +119,10 @@ __device__ __forceinline__ long long tick() {
     if constexpr (kProf) return clock64();
     return 0;
 }
+
+// outcome of a leaf visit (counted by the phase profile): no record in reach
+// of an undecided sample, records tested without deciding one, a sample decided
+constexpr uint32_t kVisitEmpty = 0, kVisitTested = 1, kVisitDecided = 2;
 
 // kinds of logged reads
 constexpr uint32_t kLogNode = 0, kLogLeaf = 1, kLogPolyNode = 2, kLogPolyLeaf = 3, kLogPoly = 4;
@@ -394,10 +398,11 @@ __device__ __forceinline__ uint32_t crossing_columns(int4 e, const Lane& s, int3
 struct PointLeaf {
     static constexpr bool kFill = false;
     static constexpr bool kCertain = true;   // boxes of points certainly cover nearby samples
-    __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
+    static constexpr bool kOutline = false;
+    __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
-            return;
+            return kVisitEmpty;
         }
         uint64_t i = (uint64_t)leaf * 32 + lane;
         log_read(p, kLogLeaf, leaf, lane);
@@ -405,7 +410,8 @@ struct PointLeaf {
         if (i < src.n) o = __ldg((const int2*)src.obj + i);
         // the exact test on the undecided samples in each point's reach
         uint32_t pm = rect_lanes(s, o.x, o.y, o.x, o.y) & s.U;
-        if (!__any_sync(kFull, pm != 0)) return;
+        if (!__any_sync(kFull, pm != 0)) return kVisitEmpty;
+        const uint32_t U_before = s.U;
         // the point relative to the block's first pixel centre; lanes in pm
         // are within reach, so the 32-bit differences below are exact
         const int32_t dxo = max(min(o.x - s.bx0, kGridHalf), -kGridHalf);
@@ -437,8 +443,10 @@ struct PointLeaf {
             }
         }
         // decided samples may be hit again: apply_cover only clears bits
-        apply_cover(s, __reduce_or_sync(kFull, c[0]), __reduce_or_sync(kFull, c[1]),
-                    __reduce_or_sync(kFull, c[2]), __reduce_or_sync(kFull, c[3]), lane);
+        const uint32_t c0 = __reduce_or_sync(kFull, c[0]), c1 = __reduce_or_sync(kFull, c[1]);
+        const uint32_t c2 = __reduce_or_sync(kFull, c[2]), c3 = __reduce_or_sync(kFull, c[3]);
+        apply_cover(s, c0, c1, c2, c3, lane);
+        return (c0 | c1 | c2 | c3) & U_before ? kVisitDecided : kVisitTested;
     }
 };
 
@@ -446,10 +454,11 @@ template <bool kScreen>
 struct SegLeaf {
     static constexpr bool kFill = false;
     static constexpr bool kCertain = false;
-    __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
+    static constexpr bool kOutline = !kScreen;   // the outline of a polygon layer
+    __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
-            return;
+            return kVisitEmpty;
         }
         uint64_t i = (uint64_t)leaf * 32 + lane;
         log_read(p, kLogLeaf, leaf, lane);
@@ -462,7 +471,8 @@ struct SegLeaf {
         }
         const int32_t sx0 = pb.x, sy0 = pb.y, sx1 = pb.z, sy1 = pb.w;
         uint32_t pm = rect_lanes(s, sx0, sy0, sx1, sy1) & s.U;
-        if (!__any_sync(kFull, pm != 0)) return;
+        if (!__any_sync(kFull, pm != 0)) return kVisitEmpty;
+        const uint32_t U_before = s.U;
         // a piece box much larger than the pixels: keep the pixels near the line
         if (__reduce_max_sync(kFull, (uint32_t)__popc(pm)) > 8u)
             pm &= line_lanes(s, mid32(sx0, sx1) - s.bx0, mid32(sy0, sy1) - s.by0, o.z - o.x, o.w - o.y);
@@ -498,8 +508,10 @@ struct SegLeaf {
                 }
             }
         }
-        apply_cover(s, __reduce_or_sync(kFull, c[0]), __reduce_or_sync(kFull, c[1]),
-                    __reduce_or_sync(kFull, c[2]), __reduce_or_sync(kFull, c[3]), lane);
+        const uint32_t c0 = __reduce_or_sync(kFull, c[0]), c1 = __reduce_or_sync(kFull, c[1]);
+        const uint32_t c2 = __reduce_or_sync(kFull, c[2]), c3 = __reduce_or_sync(kFull, c[3]);
+        apply_cover(s, c0, c1, c2, c3, lane);
+        return (c0 | c1 | c2 | c3) & U_before ? kVisitDecided : kVisitTested;
     }
 };
 
@@ -508,10 +520,11 @@ struct SegLeaf {
 struct FillLeaf {
     static constexpr bool kFill = true;
     static constexpr bool kCertain = false;
-    __device__ static void visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
+    static constexpr bool kOutline = false;
+    __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
-            return;
+            return kVisitEmpty;
         }
         uint64_t i = (uint64_t)leaf * 32 + lane;
         log_read(p, kLogPolyLeaf, leaf, lane);
@@ -523,6 +536,8 @@ struct FillLeaf {
         }
         uint32_t pm = rect_lanes(s, b.x, b.y, b.z, b.w);
         uint32_t m = __ballot_sync(kFull, (pm & s.U) != 0);
+        uint32_t outcome = m ? kVisitTested : kVisitEmpty;
+        const uint32_t U_before = s.U;
         while (m) {
             int k = __ffs(m) - 1;
             m &= m - 1;
@@ -577,6 +592,7 @@ struct FillLeaf {
                 m &= __ballot_sync(kFull, (pm & U2) != 0);
             }
         }
+        return s.U != U_before ? kVisitDecided : outcome;
     }
 };
 
@@ -631,9 +647,10 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
         __syncwarp();
         if (lvl == 1) {
             const long long t0 = tick<kProf>();
-            V::visit(p, src, child, s, lane);
+            const uint32_t how = V::visit(p, src, child, s, lane);
             prof_since<kProf>(sm, kPLeaf, t0, lane);
             prof_add<kProf>(sm, kPLeafVisits, 1, lane);
+            prof_add<kProf>(sm, how == kVisitEmpty ? kPLeafEmpty : kPLeafDecided, how != kVisitTested, lane);
             if (s.U == 0) return;
         } else {
             if (child >= src.lvl_n[lvl - 1]) {
@@ -917,7 +934,9 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         s.bx0 = X0 + (bx * kBW) * ps + (ps >> 1);
         s.by0 = Y0 + (strip * p.rows + by * kBH) * ps + (ps >> 1);
         s.R2 = (int64_t)R * R;
-        if ((V::kFill && !(p.fill_aa && !mask_mode)) || mask_mode) {
+        bool centre_only = mask_mode;
+        if constexpr (V::kFill) centre_only = mask_mode || !p.fill_aa;
+        if (centre_only) {
             s.off = 0;
             s.und = 1u;
             s.nk = 1;
@@ -930,12 +949,14 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         s.q = q;
         s.U = kFull;
         for (int k = 0; k < 4; k++) s.Uk[k] = k < s.nk ? kFull : 0u;
-        if (!V::kFill && mask_mode && p.pat_w == 0) {
-            // a MASK pixel whose centre is already filled is decided (unless a
-            // pattern may leave it transparent)
-            const uint32_t open = __ballot_sync(kFull, (sm.res[jl * kTile + i] >> kResFillShift) == 0);
-            s.U = s.Uk[0] = open;
-            s.und = (open >> lane) & 1u;
+        if constexpr (V::kOutline) {
+            if (mask_mode && p.pat_w == 0) {
+                // a MASK pixel whose centre is already filled is decided
+                // (unless a pattern may leave it transparent)
+                const uint32_t open = __ballot_sync(kFull, (sm.res[jl * kTile + i] >> kResFillShift) == 0);
+                s.U = s.Uk[0] = open;
+                s.und = (open >> lane) & 1u;
+            }
         }
         uint32_t und0 = s.und;
         {
@@ -970,9 +991,11 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                     uint32_t id = sm.fid[fb][__shfl_sync(kFull, e, k)];
                     const long long t0 = tick<kProf>();
                     if (f_level == 0) {
-                        V::visit(p, src, id, s, lane);
+                        const uint32_t how = V::visit(p, src, id, s, lane);
                         prof_since<kProf>(sm, kPLeaf, t0, lane);
                         prof_add<kProf>(sm, kPLeafVisits, 1, lane);
+                        prof_add<kProf>(sm, how == kVisitEmpty ? kPLeafEmpty : kPLeafDecided, how != kVisitTested,
+                                        lane);
                     } else {
                         descend<V, kProf>(p, sm, src, f_level, id, s, lane, warp);
                     }
@@ -1029,7 +1052,8 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
         // the column lists are rebuilt for every pass, also for an empty
         // frontier (a strip reached only by the side tree), so that the
         // blocks never read the lists of an earlier stage
-        const bool sub = V::kFill ? (p.fill_aa && !mask_mode) : !mask_mode;   // super-samples
+        bool sub = !mask_mode;   // super-samples
+        if constexpr (V::kFill) sub = !mask_mode && p.fill_aa;
         const int32_t off = sub ? ((1 << (23 - z)) >> 2) : 0;
         const long long t_bin = tick<kProf>();
         bin_frontier(sm, X0, 23 - z, (V::kFill ? 0 : R) + off, tid);
@@ -1095,84 +1119,14 @@ __device__ void decode_fill(const uint8_t* region, Smem& sm, int rows, int tid, 
     }
 }
 
-template <int kKind, bool kProf>
-__global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_render(const Params p) {
-    __shared__ Smem sm;
-    const int tid = threadIdx.x;
-    const long long t_start = tick<kProf>();
-    if constexpr (kProf) {
-        if (tid < kPN) sm.prof[tid] = 0;
-    }
-    const int rows = p.rows;
-    const uint32_t tile = blockIdx.x / p.strips;
-    const int strip = blockIdx.x % p.strips;
-    const uint32_t n = p.n_dev ? min(*p.n_dev, p.n) : p.n;
-    if (tile >= n) return;
-    hv_tile_req q = p.reqs[tile];
-    bool ok = q.z <= 19 && q.x < (1u << q.z) && q.y < (1u << q.z) && (p.R_units >= 0 || (q.r16 >= 1 && q.r16 <= 1024));
-    uint8_t* const region = p.out + (uint64_t)tile * p.tile_bytes + strip_offset(p.mode, rows, strip);
-    const bool aa_bytes = p.fill_aa && p.mode != HV_MODE_MASK;
-    if constexpr (kKind == HV_LAYER_POLYGONS)
-        decode_fill(region, sm, rows, tid, aa_bytes);
-    else
-        for (int k = tid; k < rows * kTile / 4; k += kThreads) ((uint32_t*)sm.res)[k] = 0u;
-    if (!ok) {
-        if (tid == 0 && strip == 0) atomicOr(p.status, 1u);
-    }
-    __syncthreads();
-    if (tid == 0) prof_since<kProf>(sm, kPPrologue, t_start, 0);
-    const bool mask_mode = p.mode == HV_MODE_MASK;
-    if (ok) {
-        const int z = q.z;
-        const int32_t ps = 1 << (23 - z);
-        const int32_t X0 = (int32_t)(-(int64_t)kGridHalf + (int64_t)q.x * ((int64_t)1 << (31 - z)));
-        const int32_t Y0 = (int32_t)(-(int64_t)kGridHalf + (int64_t)q.y * ((int64_t)1 << (31 - z)));
-        // at most 2^29 either way (r16 <= 1024, or the buffer limit)
-        const int32_t R = p.R_units >= 0 ? p.R_units : (int32_t)q.r16 << (19 - z);
-        const int32_t off = mask_mode ? 0 : (ps >> 2);
-        // strip sample box
-        const int32_t sx0 = X0 + (ps >> 1) - off, sx1 = X0 + (kTile - 1) * ps + (ps >> 1) + off;
-        const int32_t sy0 = Y0 + strip * rows * ps + (ps >> 1) - off;
-        const int32_t sy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1) + off;
-        const bool learned = p.use_learned != 0;
-        // Algorithm 1 over points / segments / polygon edges
-        if constexpr (kKind == HV_LAYER_POINTS)
-            stage<PointLeaf, kProf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
-                             p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
-        else if constexpr (kKind != kPolyFill)
-            stage<SegLeaf<kKind == HV_LAYER_LINES>, kProf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
-                           p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
-        // Algorithm 2 over polygon boxes and edges
-        if constexpr (kKind == kPolyFill) {
-            // the strip's centres, or its super-samples
-            const int32_t fo = aa_bytes ? (ps >> 2) : 0;
-            const int32_t cx0 = X0 + (ps >> 1) - fo, cx1 = X0 + (kTile - 1) * ps + (ps >> 1) + fo;
-            const int32_t cy0 = Y0 + strip * rows * ps + (ps >> 1) - fo;
-            const int32_t cy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1) + fo;
-            stage<FillLeaf, kProf>(p, sm, p.mtree, p.mbr_obj, p.mbr_ids, p.mside, p.mside_obj, p.mside_ids,
-                            learned ? &p.mlm : nullptr, p.mhalo, X0, Y0, strip, z, 0, mask_mode, cx0, cy0, cx1,
-                            cy1, tid);
-        }
-    }
-    // ---- encode the strip (Sec. 4.1 Render Tiles) ----
-    const long long t_enc = tick<kProf>();
-    uint8_t* out = p.out + (uint64_t)tile * p.tile_bytes;
-    // global pixel coordinates of the strip's first pixel (fill patterns)
+// The outline launch of a polygon layer encodes the strip composed over the
+// fill results: per pixel v outline samples, the fill field (centre, or the
+// anti-aliased count), a pattern texel by the global pixel coordinate.
+__device__ void encode_polygons(const Params& p, const Smem& sm, uint8_t* out, int rows, int strip,
+                                uint32_t tile, int tid) {
+    const hv_tile_req q = p.reqs[tile];
     const uint32_t gx0 = q.x * (uint32_t)kTile, gy0 = q.y * (uint32_t)kTile + (uint32_t)(strip * rows);
-    if constexpr (kKind == kPolyFill) {
-        // the fill results for the outline part, in the strip's own region
-        if (aa_bytes) {
-            for (int k = tid; k < rows * kTile / 4; k += kThreads)
-                ((uint32_t*)region)[k] = (((const uint32_t*)sm.res)[k] >> kResFillShift) & 0x07070707u;
-        } else if (tid < rows * 8) {
-            const int jl = tid >> 3, w = tid & 7;
-            uint32_t word = 0;
-            for (int b = 0; b < 32; b++)
-                if (sm.res[jl * kTile + 32 * w + b] >> kResFillShift) word |= 1u << b;
-            ((uint32_t*)region)[tid] = word;
-        }
-    } else if (p.mode == HV_MODE_MASK) {
-        // 16 rows x 8 words; word w of row j = pixels 32w .. 32w+31
+    if (p.mode == HV_MODE_MASK) {
         if (tid < rows * 8) {
             int jl = tid >> 3, w = tid & 7;
             uint32_t word = 0;
@@ -1185,29 +1139,27 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
             ((uint32_t*)out)[(strip * rows + jl) * 8 + w] = word;
         }
     } else if (p.mode == HV_MODE_COVERAGE) {
-        // rows x 256 bytes contiguous: one uint4 (16 pixels) per thread
         if (tid < rows * 16) {
-        const uint8_t* r = sm.res + tid * 16;
-        uint32_t w4[4];
-        for (int k = 0; k < 4; k++) {
-            uint32_t v = 0;
-            for (int b = 0; b < 4; b++) {
-                const uint32_t f = r[4 * k + b];
-                uint32_t fill = f >> kResFillShift;
-                if (fill && p.pat_w) {
-                    const int px = tid * 16 + 4 * k + b;
-                    if (fill_texel(p, gx0 + (px & (kTile - 1)), gy0 + px / kTile).w == 0) fill = 0;
+            const uint8_t* r = sm.res + tid * 16;
+            uint32_t w4[4];
+            for (int k = 0; k < 4; k++) {
+                uint32_t v = 0;
+                for (int b = 0; b < 4; b++) {
+                    const uint32_t f = r[4 * k + b];
+                    uint32_t fill = f >> kResFillShift;
+                    if (fill && p.pat_w) {
+                        const int px = tid * 16 + 4 * k + b;
+                        if (fill_texel(p, gx0 + (px & (kTile - 1)), gy0 + px / kTile).w == 0) fill = 0;
+                    }
+                    // anti-aliased: the fill count in bits 4-6; else bit 3 for a filled centre
+                    const uint32_t c = __popc(f & 15u) | (p.fill_aa ? fill << 4 : (fill ? 8u : 0u));
+                    v |= c << (8 * b);
                 }
-                // anti-aliased: the fill count in bits 4-6; else bit 3 for a filled centre
-                const uint32_t c = __popc(f & 15u) | (p.fill_aa ? fill << 4 : (fill ? 8u : 0u));
-                v |= c << (8 * b);
+                w4[k] = v;
             }
-            w4[k] = v;
-        }
-        ((uint4*)(out + (uint64_t)strip * rows * kTile))[tid] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            ((uint4*)(out + (uint64_t)strip * rows * kTile))[tid] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
         }
     } else {
-        // rows x 1 KB contiguous: rows / 4 rounds of one uint4 (4 pixels) per thread
         uint4* o4 = (uint4*)(out + (uint64_t)strip * rows * kTile * 4);
         for (int it = 0; it < rows / 4; it++) {
             int px = (it * kThreads + tid) * 4;
@@ -1243,6 +1195,121 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
                     rgba = (uint32_t)p.line.x | ((uint32_t)p.line.y << 8) | ((uint32_t)p.line.z << 16) | (a << 24);
                 }
                 w[b] = rgba;
+            }
+            o4[it * kThreads + tid] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+template <int kKind, bool kProf>
+__global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_render(const Params p) {
+    __shared__ Smem sm;
+    const int tid = threadIdx.x;
+    const long long t_start = tick<kProf>();
+    if constexpr (kProf) {
+        if (tid < kPN) sm.prof[tid] = 0;
+    }
+    const int rows = p.rows;
+    const uint32_t tile = blockIdx.x / p.strips;
+    const int strip = blockIdx.x % p.strips;
+    const uint32_t n = p.n_dev ? min(*p.n_dev, p.n) : p.n;
+    if (tile >= n) return;
+    hv_tile_req q = p.reqs[tile];
+    bool ok = q.z <= 19 && q.x < (1u << q.z) && q.y < (1u << q.z) && (p.R_units >= 0 || (q.r16 >= 1 && q.r16 <= 1024));
+    if constexpr (kKind == HV_LAYER_POLYGONS)
+        decode_fill(p.out + (uint64_t)tile * p.tile_bytes + strip_offset(p.mode, rows, strip), sm, rows, tid,
+                    p.fill_aa && p.mode != HV_MODE_MASK);
+    else
+        for (int k = tid; k < rows * kTile / 4; k += kThreads) ((uint32_t*)sm.res)[k] = 0u;
+    if (!ok) {
+        if (tid == 0 && strip == 0) atomicOr(p.status, 1u);
+    }
+    __syncthreads();
+    if (tid == 0) prof_since<kProf>(sm, kPPrologue, t_start, 0);
+    const bool mask_mode = p.mode == HV_MODE_MASK;
+    if (ok) {
+        const int z = q.z;
+        const int32_t ps = 1 << (23 - z);
+        const int32_t X0 = (int32_t)(-(int64_t)kGridHalf + (int64_t)q.x * ((int64_t)1 << (31 - z)));
+        const int32_t Y0 = (int32_t)(-(int64_t)kGridHalf + (int64_t)q.y * ((int64_t)1 << (31 - z)));
+        // at most 2^29 either way (r16 <= 1024, or the buffer limit)
+        int32_t R = (int32_t)q.r16 << (19 - z);
+        if (p.R_units >= 0) R = p.R_units;
+        const int32_t off = mask_mode ? 0 : (ps >> 2);
+        // strip sample box
+        const int32_t sx0 = X0 + (ps >> 1) - off, sx1 = X0 + (kTile - 1) * ps + (ps >> 1) + off;
+        const int32_t sy0 = Y0 + strip * rows * ps + (ps >> 1) - off;
+        const int32_t sy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1) + off;
+        const bool learned = p.use_learned != 0;
+        // Algorithm 1 over points / segments / polygon edges
+        if constexpr (kKind == HV_LAYER_POINTS)
+            stage<PointLeaf, kProf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
+                             p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
+        else if constexpr (kKind != kPolyFill)
+            stage<SegLeaf<kKind == HV_LAYER_LINES>, kProf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
+                           p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
+        // Algorithm 2 over polygon boxes and edges
+        if constexpr (kKind == kPolyFill) {
+            // the strip's centres, or its super-samples
+            const int32_t fo = (p.fill_aa && p.mode != HV_MODE_MASK) ? (ps >> 2) : 0;
+            const int32_t cx0 = X0 + (ps >> 1) - fo, cx1 = X0 + (kTile - 1) * ps + (ps >> 1) + fo;
+            const int32_t cy0 = Y0 + strip * rows * ps + (ps >> 1) - fo;
+            const int32_t cy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1) + fo;
+            stage<FillLeaf, kProf>(p, sm, p.mtree, p.mbr_obj, p.mbr_ids, p.mside, p.mside_obj, p.mside_ids,
+                            learned ? &p.mlm : nullptr, p.mhalo, X0, Y0, strip, z, 0, mask_mode, cx0, cy0, cx1,
+                            cy1, tid);
+        }
+    }
+    // ---- encode the strip (Sec. 4.1 Render Tiles) ----
+    const long long t_enc = tick<kProf>();
+    uint8_t* out = p.out + (uint64_t)tile * p.tile_bytes;
+    if constexpr (kKind == kPolyFill) {
+        // the fill results for the outline part, in the strip's own region
+        uint8_t* const region = out + strip_offset(p.mode, rows, strip);
+        if (p.fill_aa && p.mode != HV_MODE_MASK) {
+            for (int k = tid; k < rows * kTile / 4; k += kThreads)
+                ((uint32_t*)region)[k] = (((const uint32_t*)sm.res)[k] >> kResFillShift) & 0x07070707u;
+        } else if (tid < rows * 8) {
+            const int jl = tid >> 3, w = tid & 7;
+            uint32_t word = 0;
+            for (int b = 0; b < 32; b++)
+                if (sm.res[jl * kTile + 32 * w + b] >> kResFillShift) word |= 1u << b;
+            ((uint32_t*)region)[tid] = word;
+        }
+    } else if constexpr (kKind == HV_LAYER_POLYGONS) {
+        encode_polygons(p, sm, out, rows, strip, tile, tid);
+    } else if (p.mode == HV_MODE_MASK) {
+        // 16 rows x 8 words; word w of row j = pixels 32w .. 32w+31
+        if (tid < rows * 8) {
+            int jl = tid >> 3, w = tid & 7;
+            uint32_t word = 0;
+            for (int b = 0; b < 32; b++)
+                if (sm.res[jl * kTile + 32 * w + b] & kResCentre) word |= 1u << b;
+            ((uint32_t*)out)[(strip * rows + jl) * 8 + w] = word;
+        }
+    } else if (p.mode == HV_MODE_COVERAGE) {
+        // rows x 256 bytes contiguous: one uint4 (16 pixels) per thread
+        if (tid < rows * 16) {
+            const uint8_t* r = sm.res + tid * 16;
+            uint32_t w4[4];
+            for (int k = 0; k < 4; k++) {
+                uint32_t v = 0;
+                for (int b = 0; b < 4; b++) v |= (uint32_t)__popc(r[4 * k + b] & 15u) << (8 * b);
+                w4[k] = v;
+            }
+            ((uint4*)(out + (uint64_t)strip * rows * kTile))[tid] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+    } else {
+        // rows x 1 KB contiguous: rows / 4 rounds of one uint4 (4 pixels) per thread
+        uint4* o4 = (uint4*)(out + (uint64_t)strip * rows * kTile * 4);
+        for (int it = 0; it < rows / 4; it++) {
+            int px = (it * kThreads + tid) * 4;
+            uint32_t w[4];
+            for (int b = 0; b < 4; b++) {
+                const uint32_t v = __popc(sm.res[px + b] & 15u);
+                const uint32_t a = (255u * v + 2u) >> 2;
+                w[b] = v ? ((uint32_t)p.line.x | ((uint32_t)p.line.y << 8) | ((uint32_t)p.line.z << 16) | (a << 24))
+                         : 0u;
             }
             o4[it * kThreads + tid] = make_uint4(w[0], w[1], w[2], w[3]);
         }
@@ -1296,7 +1363,7 @@ bool fill_style_ok(const hv_fill_style* f) {
 
 int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int index_kind,
                   const hv_style* style, uint8_t* d_out, cudaStream_t stream, const RenderLog* log,
-                  const uint32_t* n_dev, int32_t R_units, const hv_fill_style* fill) {
+                  const uint32_t* n_dev, int32_t R_units, const hv_fill_style* fill, const void* pattern_dev) {
     (void)index_kind;
     if (n == 0) return HV_OK;
     Params p;
@@ -1309,11 +1376,13 @@ int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int
         }
         p.fill_aa = (fill->flags & HV_FILL_AA) ? 1 : 0;
         if (fill->pattern_w) {
+            if (!pattern_dev) {
+                set_error("a fill pattern needs its device copy");
+                return HV_EINVAL;
+            }
             p.pat_w = (int)fill->pattern_w;
             p.pat_h = (int)fill->pattern_h;
-            for (uint32_t k = 0; k < fill->pattern_w * fill->pattern_h; k++)
-                p.pattern[k] = make_uchar4(fill->pattern_rgba[4 * k], fill->pattern_rgba[4 * k + 1],
-                                           fill->pattern_rgba[4 * k + 2], fill->pattern_rgba[4 * k + 3]);
+            p.pattern = (const uchar4*)pattern_dev;
         }
     }
     p.reqs = d_reqs;

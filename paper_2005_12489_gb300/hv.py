@@ -335,7 +335,7 @@ def hv_render_tiles_counted(layer, reqs, n, mode, index_kind, style, out, out_by
 
 
 PHASE_NAMES = ["total", "prologue", "cull", "bin", "blocks_cta", "blocks_warp", "leaf", "descend", "encode",
-               "ctas", "blocks", "leaf_visits", "node_visits", "frontier_tests"]
+               "ctas", "blocks", "leaf_visits", "node_visits", "frontier_tests", "leaf_empty", "leaf_decided"]
 HV_PHASE_COUNT = 16
 
 
