@@ -265,11 +265,18 @@ __device__ __forceinline__ int64_t seg_extent(int4 s) {
     return dx > dy ? dx : dy;
 }
 
+// Histogram of the bit lengths of the segments' extents: counted per block
+// in shared memory, then added to the 65 global counters once per block
+// (one global atomic per object contended on 65 addresses).
 __global__ void k_extent_bits(const int4* segs, uint64_t n, unsigned long long* hist) {
-    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t e = seg_extent(segs[i]);
-    atomicAdd(hist + (64 - __clzll((unsigned long long)e)), 1ull);
+    __shared__ unsigned int h[65];
+    for (int k = threadIdx.x; k < 65; k += blockDim.x) h[k] = 0u;
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[64 - __clzll((unsigned long long)seg_extent(segs[i]))], 1u);
+    __syncthreads();
+    for (int k = threadIdx.x; k < 65; k += blockDim.x)
+        if (h[k]) atomicAdd(hist + k, (unsigned long long)h[k]);
 }
 
 constexpr uint32_t kMaxPieces = 4096;
@@ -327,7 +334,7 @@ int make_pieces(Ctx* c, const int4* segs, uint64_t n, Piece** out, uint64_t* n_o
     unsigned long long* hist;
     HV_TRY(tmp.get((void**)&hist, 65 * 8));
     HV_CUDA(cudaMemset(hist, 0, 65 * 8));
-    k_extent_bits<<<grid_for(n, 256), 256>>>(segs, n, hist);
+    k_extent_bits<<<(uint32_t)std::min<uint64_t>(grid_for(n, 256), 4096), 256>>>(segs, n, hist);
     unsigned long long h[65];
     HV_CUDA(cudaMemcpy(h, hist, sizeof(h), cudaMemcpyDeviceToHost));
     int shift = 12;

@@ -273,14 +273,20 @@ __global__ void k_max_u32(const uint32_t* a, uint32_t n, unsigned long long* out
 // Half-extent of each record's box (half the larger side, plus one) and a
 // histogram of its bit length; boxes are read at boxes[i * stride].
 __global__ void k_extent_hist(const int4* boxes, uint32_t stride, uint64_t n, unsigned long long* hist) {
-    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int4 b = boxes[i * stride];
-    if (b.x > b.z) return;  // empty box
-    int64_t w = (int64_t)b.z - b.x, h = (int64_t)b.w - b.y;
-    int64_t e = (w > h ? w : h) / 2 + 1;
-    int bits = 64 - __clzll((unsigned long long)e);
-    atomicAdd(hist + bits, 1ull);
+    // per-block counts in shared memory, one global add per bin and block
+    __shared__ unsigned int hs[65];
+    for (int k = threadIdx.x; k < 65; k += blockDim.x) hs[k] = 0u;
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        int4 b = boxes[i * stride];
+        if (b.x > b.z) continue;  // empty box
+        int64_t w = (int64_t)b.z - b.x, h = (int64_t)b.w - b.y;
+        int64_t e = (w > h ? w : h) / 2 + 1;
+        atomicAdd(&hs[64 - __clzll((unsigned long long)e)], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 65; k += blockDim.x)
+        if (hs[k]) atomicAdd(hist + k, (unsigned long long)hs[k]);
 }
 
 __global__ void k_mark_outliers(const int4* boxes, uint32_t stride, uint64_t n, int64_t halo, uint32_t* flag,
@@ -469,7 +475,8 @@ static int build_one(Ctx* c, Learned* L, const uint64_t* keys, uint64_t n, const
         unsigned long long* hist;
         HV_TRY(dev_alloc(c, (void**)&hist, 65 * 8));
         cudaMemset(hist, 0, 65 * 8);
-        k_extent_hist<<<blocks_for(n, 256), 256>>>(boxes, stride, n, hist);
+        k_extent_hist<<<(unsigned)(blocks_for(n, 256) < 4096 ? blocks_for(n, 256) : 4096), 256>>>(boxes, stride, n,
+                                                                                                hist);
         unsigned long long hh[65];
         cudaError_t e = cudaMemcpy(hh, hist, 65 * 8, cudaMemcpyDeviceToHost);
         dev_free(c, hist, 65 * 8);

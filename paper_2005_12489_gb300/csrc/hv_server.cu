@@ -8,7 +8,8 @@
 // free the worker forms a batch from the oldest request's (layer, mode) group,
 // admitting requests while the slot's output memory and tile count allow
 // (admission by memory), and launches it: request block H2D + render kernel
-// (a captured CUDA graph per slot and group), then the D2H of the tiles.
+// (captured CUDA graphs per slot and group: one for small batches, one for
+// full ones), then the D2H of the tiles.
 // Requests that arrive while other batches run are batched into the next free
 // slot, so their work overlaps on the device (continuous batching).  Results
 // are handed out zero-copy from the slot's pinned buffer; a slot is recycled
@@ -34,6 +35,9 @@ namespace hv {
 
 namespace {
 
+// Batches of at most this many tiles take the small-batch graph.
+constexpr uint32_t kSmallBatch = 8;
+
 double now_us() {
     return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -58,7 +62,7 @@ struct Slot {
     int outstanding = 0;          // results not yet exported
     double t_start = 0;
     int status = HV_OK;
-    std::map<uint64_t, cudaGraphExec_t> graphs;   // key: layer << 8 | mode << 4 | index
+    std::map<uint64_t, cudaGraphExec_t> graphs;   // key: size class << 40 | layer << 8 | mode << 4 | index
 };
 
 struct Done {
@@ -126,13 +130,20 @@ int launch_batch(Server* S, int k) {
     const uint64_t block_bytes = 16 + (uint64_t)S->max_batch * sizeof(hv_tile_req);
     const hv_style* style = &S->opts.style;
     if (S->opts.use_graphs) {
-        uint64_t key = ((uint64_t)r0.layer << 8) | ((uint64_t)mode << 4) | (uint64_t)index;
+        // two graphs per group: small batches launch a grid sized for a few
+        // tiles, so that each tile is split into the short strips (more CTAs
+        // per tile) that hv_render_tiles gives a small batch; larger batches
+        // launch the grid of a full batch
+        const uint32_t small = S->max_batch < kSmallBatch ? S->max_batch : kSmallBatch;
+        const uint32_t cls = n <= small ? 0u : 1u;
+        const uint32_t n_cap = cls ? S->max_batch : small;
+        uint64_t key = ((uint64_t)cls << 40) | ((uint64_t)r0.layer << 8) | ((uint64_t)mode << 4) | (uint64_t)index;
         auto it = sl.graphs.find(key);
         if (it == sl.graphs.end()) {
             cudaGraph_t g;
             HV_CUDA(cudaStreamBeginCapture(sl.st, cudaStreamCaptureModeThreadLocal));
             cudaMemcpyAsync(sl.d_block, sl.h_block, block_bytes, cudaMemcpyHostToDevice, sl.st);
-            int rc = launch_render(L, (const hv_tile_req*)(sl.d_block + 16), S->max_batch, mode, index, style,
+            int rc = launch_render(L, (const hv_tile_req*)(sl.d_block + 16), n_cap, mode, index, style,
                                    sl.d_out, sl.st, nullptr, (const uint32_t*)sl.d_block);
             cudaError_t e = cudaStreamEndCapture(sl.st, &g);
             if (rc != HV_OK) return rc;
@@ -176,6 +187,27 @@ void worker_main(Server* S) {
         bool busy = false;
         to_launch.clear();
         to_pool.clear();
+        {
+            // look before locking: only this thread moves a slot into and out
+            // of flight, so it may read those states without the lock; the lock
+            // (which submitters and pollers share) is taken only when a batch
+            // has completed or queued requests may find a free slot
+            bool completed = false, in_flight = false, free_slot = false;
+            for (auto& sl : S->slots) {
+                const int st = __atomic_load_n(&sl.state, __ATOMIC_RELAXED);
+                if (st == 0) free_slot = true;
+                if (st != 1) continue;
+                if (cudaEventQuery(sl.done) == cudaErrorNotReady)
+                    in_flight = true;
+                else
+                    completed = true;
+            }
+            const bool waiting = __atomic_load_n(&S->queued, __ATOMIC_RELAXED) != 0;
+            if (in_flight && !completed && !(waiting && free_slot)) {
+                std::this_thread::yield();
+                continue;
+            }
+        }
         {
             std::unique_lock<std::mutex> g(S->mu);
             // retire finished batches into the result pool
@@ -241,7 +273,9 @@ void worker_main(Server* S) {
                 cudaEventRecord(S->slots[k].done, S->slots[k].st);
             }
         }
-        if (busy && to_launch.empty()) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        // batches in flight: poll their events again without sleeping (a
+        // sleep's timer slack would add tens of microseconds to every batch)
+        if (busy && to_launch.empty()) std::this_thread::yield();
     }
 }
 
@@ -477,7 +511,7 @@ int hv_server_replay_detail(hv_server* srv, const hv_tile_req* reqs, const doubl
             }
             finished++;
         }
-        if (got == 0) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (got == 0) std::this_thread::yield();
     }
     *wall_us = now_us() - t0;
     return HV_OK;
