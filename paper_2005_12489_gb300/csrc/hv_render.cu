@@ -143,6 +143,10 @@ __device__ __noinline__ void check_failed(const Params& p, uint32_t code, uint64
     atomicOr(p.status, 2u);
 }
 
+// The frontier is built in two buffers that the cull alternates; the pass
+// over the blocks reads only the final one (f_buf), and the other serves the
+// warps as scratch for segment leaves (Src::seg_scratch, pair_scratch) until
+// the barrier that ends the pass.
 struct Smem {
     uint8_t res[kStripRows * kTile];
     int4 fbox[2][kFCap];
@@ -184,6 +188,8 @@ struct Src {
     const int32_t* nodes;        // node array (for the read log)
     const int32_t* const* lvl;   // lvl[l] = first node of level l
     const uint32_t* lvl_n;       // lvl_n[l] = nodes of level l
+    int4* seg_scratch;           // per warp kSegScratch int4 (segment leaves)
+    uint16_t* pair_scratch;      // per warp kPairCap pairs (segment leaves)
 };
 
 // Per-lane state of one 8 x 4 pixel block (lane l = pixel (l & 7, l >> 3)).
@@ -201,7 +207,14 @@ struct Lane {
     int32_t bx0, by0;      // warp-uniform: centre of the block's first pixel
     int32_t q;             // certain-cover half-side floor(R / sqrt 2) (points), else -1
     int L;                 // warp-uniform: log2 of the pixel size
+    bool narrow;           // warp-uniform: R + 2 off <= kNarrow (32-bit distance tests)
 };
+
+// A sample that a box reaches in Chebyshev distance lies within ext + off =
+// R + 2 off of it along each axis; with that at most kNarrow each squared
+// gap is below 2^31 and the sum of two below 2^32, so squared distances of
+// reachable samples are exact in unsigned 32-bit arithmetic.
+constexpr int32_t kNarrow = 46340;   // floor(sqrt(2^31))
 
 
 // Fold per-sample coverage masks (bit l: lane l's sample k was covered) into
@@ -241,6 +254,7 @@ __device__ __forceinline__ uint32_t rect_lanes(const Lane& s, int32_t x0, int32_
 // Does the box [x0, x1] x [y0, y1] come within Euclidean distance R of an
 // undecided sample of one of the lanes in `cand`?  Exact for every sample;
 // stops at the first that qualifies.
+template <bool kNarrowOk>
 __device__ __forceinline__ bool round_reach(const Lane& s, int32_t x0, int32_t y0, int32_t x1,
                                             int32_t y1, uint32_t cand) {
     // box edges relative to the block's first pixel centre, clamped to
@@ -248,6 +262,27 @@ __device__ __forceinline__ bool round_reach(const Lane& s, int32_t x0, int32_t y
     // 2^30 - 2^26 > R from every sample, so it never decides a gap within R
     const int32_t ax = max(min(x0 - s.bx0, kGridHalf), -kGridHalf), bx = max(min(x1 - s.bx0, kGridHalf), -kGridHalf);
     const int32_t ay = max(min(y0 - s.by0, kGridHalf), -kGridHalf), by = max(min(y1 - s.by0, kGridHalf), -kGridHalf);
+    if (kNarrowOk && s.narrow) {
+        // lanes in cand reach the box in Chebyshev distance: every gap below
+        // is at most R + 2 off
+        const uint32_t R2 = (uint32_t)s.R2;
+        while (cand) {
+            int l = __ffs(cand) - 1;
+            cand &= cand - 1;
+            const int32_t sx = (l & 7) << s.L, sy = (l >> 3) << s.L;
+            const uint32_t gxm = (uint32_t)max(max(ax - (sx - s.off), (sx - s.off) - bx), 0);
+            const uint32_t gxp = (uint32_t)max(max(ax - (sx + s.off), (sx + s.off) - bx), 0);
+            const uint32_t gym = (uint32_t)max(max(ay - (sy - s.off), (sy - s.off) - by), 0);
+            const uint32_t gyp = (uint32_t)max(max(ay - (sy + s.off), (sy + s.off) - by), 0);
+            const uint32_t xm = gxm * gxm, xp = gxp * gxp, ym = gym * gym, yp = gyp * gyp;
+            const bool h0 = (s.Uk[0] >> l) & 1u && xm + ym <= R2;
+            const bool h1 = (s.Uk[1] >> l) & 1u && xp + ym <= R2;
+            const bool h2 = (s.Uk[2] >> l) & 1u && xm + yp <= R2;
+            const bool h3 = (s.Uk[3] >> l) & 1u && xp + yp <= R2;
+            if (h0 | h1 | h2 | h3) return true;
+        }
+        return false;
+    }
     while (cand) {
         int l = __ffs(cand) - 1;
         cand &= cand - 1;
@@ -309,11 +344,11 @@ __device__ __forceinline__ void certain_cover(Lane& s, int32_t x0, int32_t y0, i
 
 // Lanes `cm` can reach and one of their undecided samples really is within
 // reach.  For the fill (R = 0, centres) the Chebyshev test is already exact.
-__device__ __forceinline__ bool reaches(const Lane& s, bool fill, uint32_t cm, int32_t x0, int32_t y0,
-                                        int32_t x1, int32_t y1) {
+template <class V>
+__device__ __forceinline__ bool reaches(const Lane& s, uint32_t cm, int32_t x0, int32_t y0, int32_t x1, int32_t y1) {
     uint32_t cand = cm & s.U;
     if (!cand) return false;
-    return fill || round_reach(s, x0, y0, x1, y1, cand);
+    return V::kFill || round_reach<V::kNarrowReach>(s, x0, y0, x1, y1, cand);
 }
 
 // Pixels of the block whose centre lies within E of the segment's line,
@@ -399,6 +434,7 @@ struct PointLeaf {
     static constexpr bool kFill = false;
     static constexpr bool kCertain = true;   // boxes of points certainly cover nearby samples
     static constexpr bool kOutline = false;
+    static constexpr bool kNarrowReach = true;   // 32-bit node tests when R + 2 off is small
     __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -418,7 +454,34 @@ struct PointLeaf {
         const int32_t dyo = max(min(o.y - s.by0, kGridHalf), -kGridHalf);
         const uint64_t R2 = (uint64_t)s.R2;
         uint32_t c[4] = {0u, 0u, 0u, 0u};
-        if (s.nk == 1) {
+        if (s.narrow) {
+            // lanes in pm lie within ext of the point along each axis, so
+            // |dx -+ off|, |dy -+ off| <= R + 2 off <= kNarrow
+            const uint32_t R2n = (uint32_t)R2;
+            if (s.nk == 1) {
+                while (pm) {
+                    int l = __ffs(pm) - 1;
+                    pm &= pm - 1;
+                    const int32_t dx = dxo - ((l & 7) << s.L), dy = dyo - ((l >> 3) << s.L);
+                    if ((uint32_t)(dx * dx) + (uint32_t)(dy * dy) <= R2n) c[0] |= 1u << l;
+                }
+            } else {
+                while (pm) {
+                    int l = __ffs(pm) - 1;
+                    pm &= pm - 1;
+                    const int32_t dx = dxo - ((l & 7) << s.L), dy = dyo - ((l >> 3) << s.L);
+                    const uint32_t xm = (uint32_t)((dx + s.off) * (dx + s.off));
+                    const uint32_t xp = (uint32_t)((dx - s.off) * (dx - s.off));
+                    const uint32_t ym = (uint32_t)((dy + s.off) * (dy + s.off));
+                    const uint32_t yp = (uint32_t)((dy - s.off) * (dy - s.off));
+                    const uint32_t bit = 1u << l;
+                    if (xm + ym <= R2n) c[0] |= bit;
+                    if (xp + ym <= R2n) c[1] |= bit;
+                    if (xm + yp <= R2n) c[2] |= bit;
+                    if (xp + yp <= R2n) c[3] |= bit;
+                }
+            }
+        } else if (s.nk == 1) {
             while (pm) {
                 int l = __ffs(pm) - 1;
                 pm &= pm - 1;
@@ -450,11 +513,22 @@ struct PointLeaf {
     }
 };
 
+// Per warp, a segment leaf's pieces (relative coordinates, and with the
+// screen the bounds of R |d|) and its (piece, pixel) pairs in reach are staged
+// in shared memory, and the warp's lanes take the pairs in turn: a leaf whose
+// few pieces in reach each reach many pixels costs ceil(pairs / 32) rounds of
+// exact tests instead of the largest piece's pixel count.
+constexpr int kSegScratch = 64;   // int4 per warp: 32 pieces + 32 screen bounds
+constexpr int kPairCap = 128;     // pairs per warp and round of staging
+static_assert(kSegScratch * kWarps <= kFCap, "segment scratch exceeds a frontier buffer");
+static_assert(kPairCap * kWarps * 2 <= kFCap * 4, "pair scratch exceeds a frontier id buffer");
+
 template <bool kScreen>
 struct SegLeaf {
     static constexpr bool kFill = false;
     static constexpr bool kCertain = false;
     static constexpr bool kOutline = !kScreen;   // the outline of a polygon layer
+    static constexpr bool kNarrowReach = false;
     __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -476,38 +550,95 @@ struct SegLeaf {
         // a piece box much larger than the pixels: keep the pixels near the line
         if (__reduce_max_sync(kFull, (uint32_t)__popc(pm)) > 8u)
             pm &= line_lanes(s, mid32(sx0, sx1) - s.bx0, mid32(sy0, sy1) - s.by0, o.z - o.x, o.w - o.y);
-        // the segment relative to the block's first pixel centre (differences
-        // of grid points fit 32 bits); 32-bit arithmetic when both endpoints
-        // are within 2^30 of it, else the absolute 64-bit test
+        // the segment relative to the block's first pixel centre (grid
+        // coordinates lie in [-2^30, 2^30), so the differences fit 32 bits);
+        // 32-bit products when both endpoints are within 2^30 of it, else the
+        // absolute 64-bit test
         const int32_t ax = o.x - s.bx0, ay = o.y - s.by0, bx = o.z - s.bx0, by = o.w - s.by0;
         const bool near = max(max(abs(ax), abs(ay)), max(abs(bx), abs(by))) <= kGridHalf;
-        const int32_t dx = o.z - o.x, dy = o.w - o.y;
-        const int64_t Ls = (int64_t)dx * dx + (int64_t)dy * dy;
+        uint32_t c[4] = {0u, 0u, 0u, 0u};
+        if (__any_sync(kFull, pm != 0 && !near)) {
+            // a segment reaching from beyond 2^30 of the block (grid-spanning
+            // edges at low zoom): each lane its own piece, absolute 64-bit tests
+            while (pm) {
+                const int l = __ffs(pm) - 1;
+                pm &= pm - 1;
+                const int32_t px = (l & 7) << s.L, py = (l >> 3) << s.L;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (k < s.nk && ((s.Uk[k] >> l) & 1u)) {
+                        const int32_t sx = s.bx0 + px + ((k & 1) ? s.off : -s.off);
+                        const int32_t sy = s.by0 + py + ((k & 2) ? s.off : -s.off);
+                        if (segment_within(o.x, o.y, o.z, o.w, sx, sy, s.R2)) c[k] |= 1u << l;
+                    }
+                }
+            }
+            return finish(s, c, U_before, lane);
+        }
+        const int warp = threadIdx.x >> 5;
+        int4* const seg = src.seg_scratch + warp * kSegScratch;
+        uint16_t* const pairs = src.pair_scratch + warp * kPairCap;
+        seg[lane] = make_int4(ax, ay, bx, by);
         // line layers screen the cross-product comparison by single-precision
         // bounds of R |d| (margins far above their rounding): |cross| <= c_lo is
         // within R, |cross| > c_hi beyond it, only the rest is compared in 128
         // bits.  The outline of polygon layers measured faster without it.
-        int64_t c_lo = -1, c_hi = INT64_MAX;   // no screen: every comparison exact
         if (kScreen) {
-            const float rs = (float)(s.ext - s.off) * sqrtf((float)Ls);
-            c_lo = (int64_t)(rs * (1.0f - 0x1p-20f)) - 1;
-            c_hi = (int64_t)(rs * (1.0f + 0x1p-20f)) + 1;
+            const int32_t dx = o.z - o.x, dy = o.w - o.y;
+            const float rs = (float)(s.ext - s.off) * sqrtf((float)((int64_t)dx * dx + (int64_t)dy * dy));
+            const long long c_lo = (long long)(rs * (1.0f - 0x1p-20f)) - 1;
+            const long long c_hi = (long long)(rs * (1.0f + 0x1p-20f)) + 1;
+            reinterpret_cast<longlong2*>(seg + 32)[lane] = make_longlong2(c_lo, c_hi);
         }
-        uint32_t c[4] = {0u, 0u, 0u, 0u};
-        while (pm) {
-            int l = __ffs(pm) - 1;
-            pm &= pm - 1;
-            const int32_t px = (l & 7) << s.L, py = (l >> 3) << s.L;
+        // the lane's pairs are numbered first .. first + popc(pm) - 1
+        const uint32_t cnt = (uint32_t)__popc(pm);
+        uint32_t incl = cnt;
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if (k < s.nk && ((s.Uk[k] >> l) & 1u)) {
-                    const int32_t sx = px + ((k & 1) ? s.off : -s.off), sy = py + ((k & 2) ? s.off : -s.off);
-                    const bool hit = near ? segment_within_rel(ax, ay, bx, by, dx, dy, Ls, c_lo, c_hi, sx, sy, s.R2)
-                                          : segment_within(o.x, o.y, o.z, o.w, s.bx0 + sx, s.by0 + sy, s.R2);
-                    if (hit) c[k] |= 1u << l;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31), first = incl - cnt;
+        const uint32_t tag = (uint32_t)lane << 5;
+        for (uint32_t w0 = 0; w0 < total; w0 += kPairCap) {
+            uint32_t m = pm, g = first - w0;   // unsigned: pairs before the round wrap above kPairCap
+            while (m) {
+                const int l = __ffs(m) - 1;
+                m &= m - 1;
+                if (g < (uint32_t)kPairCap) pairs[g] = (uint16_t)(tag | (uint32_t)l);
+                g++;
+            }
+            __syncwarp();
+            const uint32_t n = min(total - w0, (uint32_t)kPairCap);
+            for (uint32_t j = lane; j < n; j += 32) {
+                const uint32_t e = pairs[j];
+                const int l = e & 31, pc = e >> 5;
+                const int4 g4 = seg[pc];
+                long long c_lo = -1, c_hi = INT64_MAX;   // no screen: every comparison exact
+                if (kScreen) {
+                    const longlong2 b = reinterpret_cast<const longlong2*>(seg + 32)[pc];
+                    c_lo = b.x;
+                    c_hi = b.y;
+                }
+                const int32_t dx = g4.z - g4.x, dy = g4.w - g4.y;
+                const int64_t Ls = (int64_t)dx * dx + (int64_t)dy * dy;
+                const int32_t px = (l & 7) << s.L, py = (l >> 3) << s.L;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (k < s.nk && ((s.Uk[k] >> l) & 1u)) {
+                        const int32_t sx = px + ((k & 1) ? s.off : -s.off), sy = py + ((k & 2) ? s.off : -s.off);
+                        if (segment_within_rel(g4.x, g4.y, g4.z, g4.w, dx, dy, Ls, c_lo, c_hi, sx, sy, s.R2))
+                            c[k] |= 1u << l;
+                    }
                 }
             }
+            __syncwarp();
         }
+        return finish(s, c, U_before, lane);
+    }
+
+    // Fold the lanes' hits into the warp's undecided state.
+    __device__ static uint32_t finish(Lane& s, const uint32_t c[4], uint32_t U_before, int lane) {
         const uint32_t c0 = __reduce_or_sync(kFull, c[0]), c1 = __reduce_or_sync(kFull, c[1]);
         const uint32_t c2 = __reduce_or_sync(kFull, c[2]), c3 = __reduce_or_sync(kFull, c[3]);
         apply_cover(s, c0, c1, c2, c3, lane);
@@ -521,6 +652,7 @@ struct FillLeaf {
     static constexpr bool kFill = true;
     static constexpr bool kCertain = false;
     static constexpr bool kOutline = false;
+    static constexpr bool kNarrowReach = false;
     __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -599,16 +731,17 @@ struct FillLeaf {
 // Child boxes of one inner node: lane c computes the lanes child c can
 // reach, keeps it in `lm`, and the ballot selects the children to visit.
 // Point trees first decide the samples the children certainly cover.
-__device__ __forceinline__ uint32_t child_hits(const Params& p, bool fill, const Src& src,
+template <class V>
+__device__ __forceinline__ uint32_t child_hits(const Params& p, const Src& src,
                                                const int32_t* base, Lane& s, int lane, uint32_t* lm) {
     if (p.log != nullptr)
-        log_read(p, fill ? kLogPolyNode : kLogNode, (uint64_t)(base - src.nodes) >> 7, lane);
+        log_read(p, V::kFill ? kLogPolyNode : kLogNode, (uint64_t)(base - src.nodes) >> 7, lane);
     int32_t x0 = __ldg(base + lane), y0 = __ldg(base + 32 + lane);
     int32_t x1 = __ldg(base + 64 + lane), y1 = __ldg(base + 96 + lane);
     certain_cover(s, x0, y0, x1, y1, lane);
     uint32_t cm = rect_lanes(s, x0, y0, x1, y1);
     lm[lane] = cm;
-    return __ballot_sync(kFull, reaches(s, fill, cm, x0, y0, x1, y1));
+    return __ballot_sync(kFull, reaches<V>(s, cm, x0, y0, x1, y1));
 }
 
 // Depth-first descent from node `node` at level `level` (>= 1).  The stack
@@ -625,7 +758,7 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
         if (lane == 0) check_failed(p, 2, ((uint64_t)level << 40) | node);
         return;
     }
-    uint32_t m0 = child_hits(p, V::kFill, src, src.lvl[lvl] + (uint64_t)node * 128, s, lane,
+    uint32_t m0 = child_hits<V>(p, src, src.lvl[lvl] + (uint64_t)node * 128, s, lane,
                              sm.lanemask[warp][lvl]);
     prof_add<kProf>(sm, kPNodeVisits, 1, lane);
     if (s.U == 0) return;
@@ -658,7 +791,7 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
                 continue;
             }
             lvl--;
-            uint32_t hm = child_hits(p, V::kFill, src, src.lvl[lvl] + (uint64_t)child * 128, s, lane,
+            uint32_t hm = child_hits<V>(p, src, src.lvl[lvl] + (uint64_t)child * 128, s, lane,
                                      sm.lanemask[warp][lvl]);
             prof_add<kProf>(sm, kPNodeVisits, 1, lane);
             if (s.U == 0) return;
@@ -946,6 +1079,7 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
             s.nk = 4;
         }
         s.ext = (V::kFill ? 0 : R) + s.off;
+        s.narrow = (int64_t)s.ext + s.off <= kNarrow;
         s.q = q;
         s.U = kFull;
         for (int k = 0; k < 4; k++) s.Uk[k] = k < s.nk ? kFull : 0u;
@@ -983,7 +1117,7 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                         cm = rect_lanes(s, fbx.x, fbx.y, fbx.z, fbx.w);
                     }
                 }
-                uint32_t mm = __ballot_sync(kFull, reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
+                uint32_t mm = __ballot_sync(kFull, reaches<V>(s, cm, fbx.x, fbx.y, fbx.z, fbx.w));
                 prof_add<kProf>(sm, kPFrontierEntries, (unsigned long long)min(32, lcnt - c0), lane);
                 while (mm) {
                     int k = __ffs(mm) - 1;
@@ -1003,7 +1137,7 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                     prof_since<kProf>(sm, kPDescend, t0, lane);
                     // drop frontier entries that no longer reach an undecided lane
                     mm &= __ballot_sync(kFull, ((mm >> lane) & 1u) &&
-                                                   reaches(s, V::kFill, cm, fbx.x, fbx.y, fbx.z, fbx.w));
+                                                   reaches<V>(s, cm, fbx.x, fbx.y, fbx.z, fbx.w));
                 }
             }
             // objects longer than the learned index's halo live in a side tree
@@ -1059,8 +1193,11 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
         bin_frontier(sm, X0, 23 - z, (V::kFill ? 0 : R) + off, tid);
         if (tid == 0) prof_since<kProf>(sm, kPBin, t_bin, 0);
         const long long t_blocks = tick<kProf>();
-        Src src{obj, ids, t.n_obj, t.nodes, sm.lvl_base[0], sm.lvl_n[0]};
-        Src side{sobj, sids, st.n_obj, st.nodes, sm.lvl_base[1], sm.lvl_n[1]};
+        // the frontier's idle buffer: scratch for segment leaves
+        int4* const seg_scratch = sm.fbox[1 - sm.f_buf];
+        uint16_t* const pair_scratch = reinterpret_cast<uint16_t*>(sm.fid[1 - sm.f_buf]);
+        Src src{obj, ids, t.n_obj, t.nodes, sm.lvl_base[0], sm.lvl_n[0], seg_scratch, pair_scratch};
+        Src side{sobj, sids, st.n_obj, st.nodes, sm.lvl_base[1], sm.lvl_n[1], seg_scratch, pair_scratch};
         blocks_pass<V, kProf>(p, sm, src, side, side_hit ? st.top : 0, X0, Y0, strip, z, R, mask_mode, tid);
         __syncthreads();
         if (tid == 0) prof_since<kProf>(sm, kPBlocksCta, t_blocks, 0);
