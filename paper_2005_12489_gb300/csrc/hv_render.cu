@@ -351,6 +351,38 @@ __device__ __forceinline__ bool reaches(const Lane& s, uint32_t cm, int32_t x0, 
     return V::kFill || round_reach<V::kNarrowReach>(s, x0, y0, x1, y1, cand);
 }
 
+// One box against the lanes' own undecided samples (lanes in `lanes` only,
+// each lane its four samples, no loop): whether the box comes within R of
+// any of them.  The same exact test as round_reach, transposed.
+template <bool kNarrowOk>
+__device__ __forceinline__ bool box_reach_lanes(const Lane& s, int32_t x0, int32_t y0, int32_t x1, int32_t y1,
+                                                uint32_t lanes, int lane) {
+    bool hit = false;
+    if ((lanes >> lane) & 1u) {
+        const int32_t ax = max(min(x0 - s.bx0, kGridHalf), -kGridHalf), bx = max(min(x1 - s.bx0, kGridHalf), -kGridHalf);
+        const int32_t ay = max(min(y0 - s.by0, kGridHalf), -kGridHalf), by = max(min(y1 - s.by0, kGridHalf), -kGridHalf);
+        const int32_t sx = (lane & 7) << s.L, sy = (lane >> 3) << s.L;
+        const uint32_t gxm = (uint32_t)max(max(ax - (sx - s.off), (sx - s.off) - bx), 0);
+        const uint32_t gxp = (uint32_t)max(max(ax - (sx + s.off), (sx + s.off) - bx), 0);
+        const uint32_t gym = (uint32_t)max(max(ay - (sy - s.off), (sy - s.off) - by), 0);
+        const uint32_t gyp = (uint32_t)max(max(ay - (sy + s.off), (sy + s.off) - by), 0);
+        if (kNarrowOk && s.narrow) {
+            // the lane is in the box's Chebyshev reach: gaps at most R + 2 off
+            const uint32_t R2 = (uint32_t)s.R2;
+            const uint32_t xm = gxm * gxm, xp = gxp * gxp, ym = gym * gym, yp = gyp * gyp;
+            hit = ((s.und & 1u) && xm + ym <= R2) || ((s.und & 2u) && xp + ym <= R2) ||
+                  ((s.und & 4u) && xm + yp <= R2) || ((s.und & 8u) && xp + yp <= R2);
+        } else {
+            const uint64_t R2 = (uint64_t)s.R2;
+            const uint64_t xm = (uint64_t)gxm * gxm, xp = (uint64_t)gxp * gxp;
+            const uint64_t ym = (uint64_t)gym * gym, yp = (uint64_t)gyp * gyp;
+            hit = ((s.und & 1u) && xm + ym <= R2) || ((s.und & 2u) && xp + ym <= R2) ||
+                  ((s.und & 4u) && xm + yp <= R2) || ((s.und & 8u) && xp + yp <= R2);
+        }
+    }
+    return __any_sync(kFull, hit);
+}
+
 // Pixels of the block whose centre lies within E of the segment's line,
 // E = R + 2 off + slack >= R + off * sqrt 2 (a covered sample's pixel centre
 // is that close): in pixel row r the centres (c ps, r ps), relative to the
@@ -435,6 +467,9 @@ struct PointLeaf {
     static constexpr bool kCertain = true;   // boxes of points certainly cover nearby samples
     static constexpr bool kOutline = false;
     static constexpr bool kNarrowReach = true;   // 32-bit node tests when R + 2 off is small
+    // frontier entries and children filtered exactly when listed, by their
+    // Chebyshev reach when taken (see blocks_pass)
+    static constexpr bool kExactWhenTaken = false, kScanChebyshev = false, kChildChebyshev = false;
     __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -529,6 +564,9 @@ struct SegLeaf {
     static constexpr bool kCertain = false;
     static constexpr bool kOutline = !kScreen;   // the outline of a polygon layer
     static constexpr bool kNarrowReach = false;
+    // frontier entries listed by their Chebyshev reach, tested exactly when
+    // taken (measured faster for segments, slower for points)
+    static constexpr bool kExactWhenTaken = true, kScanChebyshev = true, kChildChebyshev = false;
     __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -653,6 +691,8 @@ struct FillLeaf {
     static constexpr bool kCertain = false;
     static constexpr bool kOutline = false;
     static constexpr bool kNarrowReach = false;
+    // R = 0 at the centres: the Chebyshev test is already exact
+    static constexpr bool kExactWhenTaken = false, kScanChebyshev = false, kChildChebyshev = false;
     __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -741,7 +781,10 @@ __device__ __forceinline__ uint32_t child_hits(const Params& p, const Src& src,
     certain_cover(s, x0, y0, x1, y1, lane);
     uint32_t cm = rect_lanes(s, x0, y0, x1, y1);
     lm[lane] = cm;
-    return __ballot_sync(kFull, reaches<V>(s, cm, x0, y0, x1, y1));
+    if constexpr (V::kChildChebyshev)
+        return __ballot_sync(kFull, (cm & s.U) != 0u);
+    else
+        return __ballot_sync(kFull, reaches<V>(s, cm, x0, y0, x1, y1));
 }
 
 // Depth-first descent from node `node` at level `level` (>= 1).  The stack
@@ -778,6 +821,13 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
         __syncwarp();
         stk_mask[lvl] = m & (m - 1);
         __syncwarp();
+        if constexpr (V::kChildChebyshev) {
+            // listed by its Chebyshev reach only: the exact test now
+            const int32_t* nb = src.lvl[lvl] + (uint64_t)stk_node[lvl] * 128;
+            if (!box_reach_lanes<V::kNarrowReach>(s, __ldg(nb + c), __ldg(nb + 32 + c), __ldg(nb + 64 + c),
+                                                  __ldg(nb + 96 + c), sm.lanemask[warp][lvl][c] & s.U, lane))
+                continue;
+        }
         if (lvl == 1) {
             const long long t0 = tick<kProf>();
             const uint32_t how = V::visit(p, src, child, s, lane);
@@ -1117,12 +1167,23 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                         cm = rect_lanes(s, fbx.x, fbx.y, fbx.z, fbx.w);
                     }
                 }
-                uint32_t mm = __ballot_sync(kFull, reaches<V>(s, cm, fbx.x, fbx.y, fbx.z, fbx.w));
+                uint32_t mm;
+                if constexpr (V::kScanChebyshev)
+                    mm = __ballot_sync(kFull, (cm & s.U) != 0u);
+                else
+                    mm = __ballot_sync(kFull, reaches<V>(s, cm, fbx.x, fbx.y, fbx.z, fbx.w));
                 prof_add<kProf>(sm, kPFrontierEntries, (unsigned long long)min(32, lcnt - c0), lane);
                 while (mm) {
                     int k = __ffs(mm) - 1;
                     mm &= mm - 1;
-                    uint32_t id = sm.fid[fb][__shfl_sync(kFull, e, k)];
+                    const int ek = __shfl_sync(kFull, e, k);
+                    if constexpr (V::kExactWhenTaken) {
+                        const int4 bk = sm.fbox[fb][ek];
+                        if (!box_reach_lanes<V::kNarrowReach>(s, bk.x, bk.y, bk.z, bk.w,
+                                                              __shfl_sync(kFull, cm, k) & s.U, lane))
+                            continue;
+                    }
+                    uint32_t id = sm.fid[fb][ek];
                     const long long t0 = tick<kProf>();
                     if (f_level == 0) {
                         const uint32_t how = V::visit(p, src, id, s, lane);
@@ -1136,8 +1197,11 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                     // everything below the frontier (leaves included)
                     prof_since<kProf>(sm, kPDescend, t0, lane);
                     // drop frontier entries that no longer reach an undecided lane
-                    mm &= __ballot_sync(kFull, ((mm >> lane) & 1u) &&
-                                                   reaches<V>(s, cm, fbx.x, fbx.y, fbx.z, fbx.w));
+                    if constexpr (V::kExactWhenTaken)
+                        mm &= __ballot_sync(kFull, ((mm >> lane) & 1u) && (cm & s.U) != 0u);
+                    else
+                        mm &= __ballot_sync(kFull, ((mm >> lane) & 1u) &&
+                                                       reaches<V>(s, cm, fbx.x, fbx.y, fbx.z, fbx.w));
                 }
             }
             // objects longer than the learned index's halo live in a side tree
