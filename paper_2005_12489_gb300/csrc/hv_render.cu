@@ -470,6 +470,7 @@ struct PointLeaf {
     // frontier entries and children filtered exactly when listed, by their
     // Chebyshev reach when taken (see blocks_pass)
     static constexpr bool kExactWhenTaken = false, kScanChebyshev = false, kChildChebyshev = false;
+    static constexpr bool kOneVisitSite = false;
     __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -567,6 +568,7 @@ struct SegLeaf {
     // frontier entries listed by their Chebyshev reach, tested exactly when
     // taken (measured faster for segments, slower for points)
     static constexpr bool kExactWhenTaken = true, kScanChebyshev = true, kChildChebyshev = false;
+    static constexpr bool kOneVisitSite = !kScreen;   // polygon outlines
     __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -693,6 +695,7 @@ struct FillLeaf {
     static constexpr bool kNarrowReach = false;
     // R = 0 at the centres: the Chebyshev test is already exact
     static constexpr bool kExactWhenTaken = false, kScanChebyshev = false, kChildChebyshev = false;
+    static constexpr bool kOneVisitSite = true;
     __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -849,6 +852,78 @@ __device__ void descend(const Params& p, Smem& sm, const Src& src, int level, ui
             stk_mask[lvl] = hm;
             __syncwarp();
         }
+    }
+}
+
+// The same descent for visitors with kOneVisitSite, also from a leaf (level
+// 0, a frontier of leaves): their leaves are reached only through the one
+// visit below, so the leaf code exists once in the kernel.  The polygon
+// kernels measured faster that way (instruction fetch); points and line
+// layers slower, so they keep the form above and visit a frontier of
+// leaves directly.
+template <class V, bool kProf>
+__device__ void descend_one_site(const Params& p, Smem& sm, const Src& src, int level, uint32_t node, Lane& s,
+                        int lane, int warp) {
+    uint32_t* stk_node = sm.stk_node[warp];
+    uint32_t* stk_mask = sm.stk_mask[warp];
+    int lvl = level;
+    if (level < 0 || level > kMaxLevels || (level > 0 && node >= src.lvl_n[level])) {
+        if (lane == 0) check_failed(p, 2, ((uint64_t)level << 40) | node);
+        return;
+    }
+    uint32_t leaf = node;
+    if (level > 0) {
+        uint32_t m0 = child_hits<V>(p, src, src.lvl[lvl] + (uint64_t)node * 128, s, lane, sm.lanemask[warp][lvl]);
+        prof_add<kProf>(sm, kPNodeVisits, 1, lane);
+        if (s.U == 0) return;
+        stk_node[lvl] = node;
+        stk_mask[lvl] = m0;
+        __syncwarp();
+    }
+    while (true) {
+        if (lvl > 0) {
+            uint32_t m = stk_mask[lvl];
+            m = __ballot_sync(kFull, ((m >> lane) & 1u) && (sm.lanemask[warp][lvl][lane] & s.U));
+            if (m == 0) {
+                if (lvl == level) break;
+                lvl++;
+                continue;
+            }
+            int c = __ffs(m) - 1;
+            uint32_t child = stk_node[lvl] * 32u + (uint32_t)c;
+            __syncwarp();
+            stk_mask[lvl] = m & (m - 1);
+            __syncwarp();
+            if constexpr (V::kChildChebyshev) {
+                // listed by its Chebyshev reach only: the exact test now
+                const int32_t* nb = src.lvl[lvl] + (uint64_t)stk_node[lvl] * 128;
+                if (!box_reach_lanes<V::kNarrowReach>(s, __ldg(nb + c), __ldg(nb + 32 + c), __ldg(nb + 64 + c),
+                                                      __ldg(nb + 96 + c), sm.lanemask[warp][lvl][c] & s.U, lane))
+                    continue;
+            }
+            if (lvl > 1) {
+                if (child >= src.lvl_n[lvl - 1]) {
+                    if (lane == 0) check_failed(p, 3, ((uint64_t)(lvl - 1) << 40) | child);
+                    continue;
+                }
+                lvl--;
+                uint32_t hm = child_hits<V>(p, src, src.lvl[lvl] + (uint64_t)child * 128, s, lane,
+                                            sm.lanemask[warp][lvl]);
+                prof_add<kProf>(sm, kPNodeVisits, 1, lane);
+                if (s.U == 0) return;
+                stk_node[lvl] = child;
+                stk_mask[lvl] = hm;
+                __syncwarp();
+                continue;
+            }
+            leaf = child;
+        }
+        const long long t0 = tick<kProf>();
+        const uint32_t how = V::visit(p, src, leaf, s, lane);
+        prof_since<kProf>(sm, kPLeaf, t0, lane);
+        prof_add<kProf>(sm, kPLeafVisits, 1, lane);
+        prof_add<kProf>(sm, how == kVisitEmpty ? kPLeafEmpty : kPLeafDecided, how != kVisitTested, lane);
+        if (s.U == 0 || level == 0) return;
     }
 }
 
@@ -1185,7 +1260,9 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
                     }
                     uint32_t id = sm.fid[fb][ek];
                     const long long t0 = tick<kProf>();
-                    if (f_level == 0) {
+                    if constexpr (V::kOneVisitSite) {
+                        descend_one_site<V, kProf>(p, sm, src, f_level, id, s, lane, warp);
+                    } else if (f_level == 0) {
                         const uint32_t how = V::visit(p, src, id, s, lane);
                         prof_since<kProf>(sm, kPLeaf, t0, lane);
                         prof_add<kProf>(sm, kPLeafVisits, 1, lane);
@@ -1207,7 +1284,10 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
             // objects longer than the learned index's halo live in a side tree
             if (side_top > 0 && s.U) {
                 const long long t0 = tick<kProf>();
-                descend<V, kProf>(p, sm, side, side_top, 0, s, lane, warp);
+                if constexpr (V::kOneVisitSite)
+                    descend_one_site<V, kProf>(p, sm, side, side_top, 0, s, lane, warp);
+                else
+                    descend<V, kProf>(p, sm, side, side_top, 0, s, lane, warp);
                 prof_since<kProf>(sm, kPDescend, t0, lane);
             }
         }
@@ -1280,11 +1360,12 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
 // the instruction cache; fused, the polygon kernel measured 40% slower.
 constexpr int kPolyFill = 3;
 
-// CTAs per SM: points keep four (their traversal fits 64 registers); the
-// segment and fill paths run faster with the registers of three.
+// CTAs per SM: four (64 registers) for every kind, measured best for each
+// since the segment leaves share their pairs over the lanes (the segment
+// kernel keeps a 16-byte spill and still runs 8% faster than with three).
 template <int kKind>
 struct KindTraits {
-    static constexpr int kBlocksPerSM = kKind == HV_LAYER_POINTS ? 4 : 3;
+    static constexpr int kBlocksPerSM = 4;
 };
 
 // The pattern texel of global pixel (gx, gy).
