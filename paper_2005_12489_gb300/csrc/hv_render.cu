@@ -549,8 +549,8 @@ struct PointLeaf {
     }
 };
 
-// Per warp, a segment leaf's pieces (relative coordinates, and with the
-// screen the bounds of R |d|) and its (piece, pixel) pairs in reach are staged
+// Per warp, a segment leaf's pieces (relative coordinates and the screen
+// bounds of R |d|) and its (piece, pixel) pairs in reach are staged
 // in shared memory, and the warp's lanes take the pairs in turn: a leaf whose
 // few pieces in reach each reach many pixels costs ceil(pairs / 32) rounds of
 // exact tests instead of the largest piece's pixel count.
@@ -559,16 +559,16 @@ constexpr int kPairCap = 128;     // pairs per warp and round of staging
 static_assert(kSegScratch * kWarps <= kFCap, "segment scratch exceeds a frontier buffer");
 static_assert(kPairCap * kWarps * 2 <= kFCap * 4, "pair scratch exceeds a frontier id buffer");
 
-template <bool kScreen>
+template <bool kLineLayer>
 struct SegLeaf {
     static constexpr bool kFill = false;
     static constexpr bool kCertain = false;
-    static constexpr bool kOutline = !kScreen;   // the outline of a polygon layer
+    static constexpr bool kOutline = !kLineLayer;   // the outline of a polygon layer
     static constexpr bool kNarrowReach = false;
     // frontier entries listed by their Chebyshev reach, tested exactly when
     // taken (measured faster for segments, slower for points)
     static constexpr bool kExactWhenTaken = true, kScanChebyshev = true, kChildChebyshev = false;
-    static constexpr bool kOneVisitSite = !kScreen;   // polygon outlines
+    static constexpr bool kOneVisitSite = !kLineLayer;   // polygon outlines
     __device__ static uint32_t visit(const Params& p, const Src& src, uint32_t leaf, Lane& s, int lane) {
         if ((uint64_t)leaf * 32 >= src.n) {
             if (lane == 0) check_failed(p, 4, leaf);
@@ -619,11 +619,11 @@ struct SegLeaf {
         int4* const seg = src.seg_scratch + warp * kSegScratch;
         uint16_t* const pairs = src.pair_scratch + warp * kPairCap;
         seg[lane] = make_int4(ax, ay, bx, by);
-        // line layers screen the cross-product comparison by single-precision
-        // bounds of R |d| (margins far above their rounding): |cross| <= c_lo is
+        // the cross-product comparison is screened by single-precision bounds
+        // of R |d| (margins far above their rounding): |cross| <= c_lo is
         // within R, |cross| > c_hi beyond it, only the rest is compared in 128
-        // bits.  The outline of polygon layers measured faster without it.
-        if (kScreen) {
+        // bits
+        {
             const int32_t dx = o.z - o.x, dy = o.w - o.y;
             const float rs = (float)(s.ext - s.off) * sqrtf((float)((int64_t)dx * dx + (int64_t)dy * dy));
             const long long c_lo = (long long)(rs * (1.0f - 0x1p-20f)) - 1;
@@ -654,12 +654,8 @@ struct SegLeaf {
                 const uint32_t e = pairs[j];
                 const int l = e & 31, pc = e >> 5;
                 const int4 g4 = seg[pc];
-                long long c_lo = -1, c_hi = INT64_MAX;   // no screen: every comparison exact
-                if (kScreen) {
-                    const longlong2 b = reinterpret_cast<const longlong2*>(seg + 32)[pc];
-                    c_lo = b.x;
-                    c_hi = b.y;
-                }
+                const longlong2 scr = reinterpret_cast<const longlong2*>(seg + 32)[pc];
+                const long long c_lo = scr.x, c_hi = scr.y;
                 const int32_t dx = g4.z - g4.x, dy = g4.w - g4.y;
                 const int64_t Ls = (int64_t)dx * dx + (int64_t)dy * dy;
                 const int32_t px = (l & 7) << s.L, py = (l >> 3) << s.L;
@@ -1361,8 +1357,9 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
 constexpr int kPolyFill = 3;
 
 // CTAs per SM: four (64 registers) for every kind, measured best for each
-// since the segment leaves share their pairs over the lanes (the segment
-// kernel keeps a 16-byte spill and still runs 8% faster than with three).
+// since the segment leaves share their pairs over the lanes (the line and
+// outline kernels keep a 12-16 byte spill and still run faster than with
+// three).
 template <int kKind>
 struct KindTraits {
     static constexpr int kBlocksPerSM = 4;
