@@ -40,6 +40,8 @@ constexpr int kBlocksX = kTile / kBW;
 constexpr int kFCap = 512;
 constexpr int kBucketCap = 2048;   // keeps the static shared memory under 48 KiB
 constexpr int kCullCells = 64;     // learned cull: at most this many Hilbert cells per strip
+constexpr int kCullSub = kThreads / kCullCells;   // threads per cell
+static_assert(kCullSub >= 2 && kCullSub <= 32 && (kCullSub & (kCullSub - 1)) == 0, "cell threads within a warp");
 constexpr int kMaxPattern = 16;    // fill patterns: at most 16 x 16 texels
 
 // result bits per pixel: bits 0-3 the outline's super-samples, bit 4 the
@@ -1039,22 +1041,27 @@ __device__ void learned_cull(const Params& p, const TreeArg& t, const LModel& m,
     }
     const int64_t gx0 = (x0 + kGridHalf) >> k, gy0 = (y0 + kGridHalf) >> k;
     const int nx = (int)(((x1 + kGridHalf) >> k) - gx0 + 1), ny = (int)(((y1 + kGridHalf) >> k) - gy0 + 1);
-    uint64_t a = 1, b = 0;   // leaf range of this thread's cell (empty)
-    if (tid < nx * ny) {
-        int64_t cx = ((gx0 + tid % nx) << k) - kGridHalf, cy = ((gy0 + tid / nx) << k) - kGridHalf;
+    // kCullSub neighbouring threads (one warp) per cell: its two lookups run
+    // at once on two of them, and they share its entries below
+    const int cell = tid / kCullSub, sub = tid % kCullSub, lane = tid & 31;
+    uint64_t pos = 0;
+    if (cell < nx * ny && sub < 2) {
+        int64_t cx = ((gx0 + cell % nx) << k) - kGridHalf, cy = ((gy0 + cell / nx) << k) - kGridHalf;
         uint64_t span = (k >= 31) ? (1ull << 62) : (1ull << (2 * k));
         uint64_t klo = (k >= 31) ? 0ull : (hilbert_key((int32_t)cx, (int32_t)cy) & ~(span - 1));
         bool fb;
-        uint64_t plo = learn_lower_bound(m, klo, &fb);
-        uint64_t phi = learn_lower_bound(m, klo + span, &fb);
-        if (phi > plo) {
-            a = plo >> 5;
-            b = (phi - 1) >> 5;
-        }
+        pos = learn_lower_bound(m, sub == 0 ? klo : klo + span, &fb);
+    }
+    const uint64_t plo = __shfl_sync(kFull, pos, lane & ~(kCullSub - 1));
+    const uint64_t phi = __shfl_sync(kFull, pos, (lane & ~(kCullSub - 1)) + 1);
+    uint64_t a = 1, b = 0;   // leaf range of this thread's cell (empty)
+    if (cell < nx * ny && phi > plo) {
+        a = plo >> 5;
+        b = (phi - 1) >> 5;
     }
     // entries per level: the leaves [a, b] span (b >> 5l) - (a >> 5l) + 1 subtrees of level l
     for (int l = 0; l < t.top; l++)
-        if (a <= b) atomicAdd(&cnt[l], (unsigned long long)((b >> (5 * l)) - (a >> (5 * l)) + 1));
+        if (sub == 0 && a <= b) atomicAdd(&cnt[l], (unsigned long long)((b >> (5 * l)) - (a >> (5 * l)) + 1));
     __syncthreads();
     int lvl = t.top;   // no level fits: fall back to the root alone
     for (int l = 0; l < t.top; l++)
@@ -1075,7 +1082,7 @@ __device__ void learned_cull(const Params& p, const TreeArg& t, const LModel& m,
         const int32_t* par = sm.lvl_base[0][lvl + 1];
         const bool inside = (e1 >> 5) < sm.lvl_n[0][lvl + 1];
         if (!inside) check_failed(p, 9, ((uint64_t)lvl << 40) | (e1 & ((1ull << 40) - 1)));
-        for (uint64_t e = e0; inside && e <= e1; e++) {
+        for (uint64_t e = e0 + sub; inside && e <= e1; e += kCullSub) {
             const int32_t* nd = par + (e >> 5) * 128;
             int c = (int)(e & 31);
             int4 bb = make_int4(__ldg(nd + c), __ldg(nd + 32 + c), __ldg(nd + 64 + c), __ldg(nd + 96 + c));
