@@ -551,12 +551,12 @@ struct PointLeaf {
     }
 };
 
-// Per warp, a segment leaf's pieces (relative coordinates and the screen
-// bounds of R |d|) and its (piece, pixel) pairs in reach are staged
+// Per warp, a segment leaf's pieces (their screen parameters, below) and its
+// (piece, pixel) pairs in reach are staged
 // in shared memory, and the warp's lanes take the pairs in turn: a leaf whose
 // few pieces in reach each reach many pixels costs ceil(pairs / 32) rounds of
 // exact tests instead of the largest piece's pixel count.
-constexpr int kSegScratch = 64;   // int4 per warp: 32 pieces + 32 screen bounds
+constexpr int kSegScratch = 64;   // 16-byte slots per warp: two per piece
 constexpr int kPairCap = 128;     // pairs per warp and round of staging
 static_assert(kSegScratch * kWarps <= kFCap, "segment scratch exceeds a frontier buffer");
 static_assert(kPairCap * kWarps * 2 <= kFCap * 4, "pair scratch exceeds a frontier id buffer");
@@ -620,17 +620,37 @@ struct SegLeaf {
         const int warp = threadIdx.x >> 5;
         int4* const seg = src.seg_scratch + warp * kSegScratch;
         uint16_t* const pairs = src.pair_scratch + warp * kPairCap;
-        seg[lane] = make_int4(ax, ay, bx, by);
-        // the cross-product comparison is screened by single-precision bounds
-        // of R |d| (margins far above their rounding): |cross| <= c_lo is
-        // within R, |cross| > c_hi beyond it, only the rest is compared in 128
-        // bits
+        // single-precision screen of the distance test.  Per piece, from exact
+        // int64 values rounded once: the unit direction m = d / |d|, the
+        // line's offset c0 = (d x a) / |d| and the projection offset
+        // e0 = (d . a) / |d|, so that a sample s (relative to the block, its
+        // coordinates exact in single precision) lies at signed distance
+        // m x s - c0 from the line and at m . s - e0 along it from a; the
+        // distance to the closed segment is then |(along - clamp(along, 0,
+        // |d|), across)|.  Every rounding is bounded by 8 units in the last
+        // place of the magnitudes involved (|s| <= 8 ps, |c0|, |e0|, |d|, R);
+        // E1 takes 64 of them plus 2 grid units, and the squared thresholds
+        // another 2^-20: a sample closer than R - E1 is within R, one farther
+        // than R + E1 beyond it, and only the rest is decided exactly.
         {
             const int32_t dx = o.z - o.x, dy = o.w - o.y;
-            const float rs = (float)(s.ext - s.off) * sqrtf((float)((int64_t)dx * dx + (int64_t)dy * dy));
-            const long long c_lo = (long long)(rs * (1.0f - 0x1p-20f)) - 1;
-            const long long c_hi = (long long)(rs * (1.0f + 0x1p-20f)) + 1;
-            reinterpret_cast<longlong2*>(seg + 32)[lane] = make_longlong2(c_lo, c_hi);
+            const int64_t Ls = (int64_t)dx * dx + (int64_t)dy * dy;
+            float mx = 1.f, my = 0.f, c0 = (float)ay, e0 = (float)ax, D = 0.f;   // a point: any direction
+            if (Ls > 0) {
+                D = sqrtf((float)Ls);
+                const float inv = 1.0f / D;
+                mx = (float)dx * inv;
+                my = (float)dy * inv;
+                c0 = (float)((int64_t)dx * ay - (int64_t)dy * ax) * inv;
+                e0 = (float)((int64_t)dx * ax + (int64_t)dy * ay) * inv;
+            }
+            const float fR = (float)(s.ext - s.off);
+            const float E1 = fmaf(0x1p-18f, 32.f * (float)(1 << s.L) + fabsf(c0) + fabsf(e0) + D + fR, 2.f);
+            const float lo = fR - E1, hi = fR + E1;
+            const float lo2 = lo > 0.f ? lo * lo * (1.f - 0x1p-20f) : -1.f;
+            const float hi2 = hi * hi * (1.f + 0x1p-20f);
+            reinterpret_cast<float4*>(seg)[lane] = make_float4(mx, my, c0, e0);
+            reinterpret_cast<float4*>(seg + 32)[lane] = make_float4(D, lo2, hi2, 0.f);
         }
         // the lane's pairs are numbered first .. first + popc(pm) - 1
         const uint32_t cnt = (uint32_t)__popc(pm);
@@ -655,18 +675,34 @@ struct SegLeaf {
             for (uint32_t j = lane; j < n; j += 32) {
                 const uint32_t e = pairs[j];
                 const int l = e & 31, pc = e >> 5;
-                const int4 g4 = seg[pc];
-                const longlong2 scr = reinterpret_cast<const longlong2*>(seg + 32)[pc];
-                const long long c_lo = scr.x, c_hi = scr.y;
-                const int32_t dx = g4.z - g4.x, dy = g4.w - g4.y;
-                const int64_t Ls = (int64_t)dx * dx + (int64_t)dy * dy;
-                const int32_t px = (l & 7) << s.L, py = (l >> 3) << s.L;
+                const float4 A = reinterpret_cast<const float4*>(seg)[pc];
+                const float4 B = reinterpret_cast<const float4*>(seg + 32)[pc];
+                // the pixel's column and row as exact floats (2^23 + c - 2^23)
+                const float col = __int_as_float(0x4B000000 | (l & 7)) - 8388608.f;
+                const float row = __int_as_float(0x4B000000 | (l >> 3)) - 8388608.f;
+                const float fps = (float)(1 << s.L), foff = (float)s.off;
+                const float sxs[2] = {fmaf(col, fps, -foff), fmaf(col, fps, foff)};
+                const float sys[2] = {fmaf(row, fps, -foff), fmaf(row, fps, foff)};
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     if (k < s.nk && ((s.Uk[k] >> l) & 1u)) {
-                        const int32_t sx = px + ((k & 1) ? s.off : -s.off), sy = py + ((k & 2) ? s.off : -s.off);
-                        if (segment_within_rel(g4.x, g4.y, g4.z, g4.w, dx, dy, Ls, c_lo, c_hi, sx, sy, s.R2))
-                            c[k] |= 1u << l;
+                        const float sx = sxs[k & 1], sy = sys[k >> 1];
+                        const float across = fmaf(A.x, sy, -fmaf(A.y, sx, A.z));
+                        const float along = fmaf(A.x, sx, fmaf(A.y, sy, -A.w));
+                        const float u = along - fminf(fmaxf(along, 0.f), B.x);
+                        const float q = fmaf(u, u, across * across);
+                        bool hit = q < B.y;
+                        if (!hit && q <= B.z) {
+                            // within the margin: the exact test on the piece's segment
+                            const int4 og = __ldg((const int4*)src.obj + 2 * ((uint64_t)leaf * 32 + pc));
+                            const int32_t gx = og.x - s.bx0, gy = og.y - s.by0, hx = og.z - s.bx0, hy = og.w - s.by0;
+                            const int32_t dx = og.z - og.x, dy = og.w - og.y;
+                            const int32_t isx = ((l & 7) << s.L) + ((k & 1) ? s.off : -s.off);
+                            const int32_t isy = ((l >> 3) << s.L) + ((k & 2) ? s.off : -s.off);
+                            hit = segment_within_rel(gx, gy, hx, hy, dx, dy, (int64_t)dx * dx + (int64_t)dy * dy, -1,
+                                                     INT64_MAX, isx, isy, s.R2);
+                        }
+                        if (hit) c[k] |= 1u << l;
                     }
                 }
             }
