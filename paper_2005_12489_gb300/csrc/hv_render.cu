@@ -10,7 +10,9 @@
 //   the centre an odd number of times.
 //
 // Work decomposition.  One CTA (8 warps) renders a strip of 256 x rows pixels
-// of one tile (rows = 16 for large batches, 8 or 4 for small ones).  The CTA
+// of one tile (rows = 16 for large batches, 8 or 4 for small ones; batches
+// too small to fill the GPU even then split each 4-row strip into 2 or 4
+// column parts, one CTA each).  The CTA
 // first culls the R-tree (or, with the learned index, the subtrees of the
 // key ranges the model finds) against the strip's box expanded by R, breadth
 // first, into a frontier of at most kFCap nodes in shared memory (the deepest
@@ -64,6 +66,9 @@ struct Params {
     uint32_t n;
     int rows;                   // pixel rows per CTA strip: 4, 8 or 16
     int strips;                 // strips per tile (256 / rows)
+    int cols;                   // pixel columns per CTA: 256, or 128 / 64 for batches too small to fill the GPU
+    int parts;                  // CTAs per strip (256 / cols)
+    int col_shift;              // log2(cols / 8): block columns per CTA as a shift
     const uint32_t* n_dev;      // if set, the batch size is min(*n_dev, n) (graph launches)
     int mode;
     int kind;
@@ -133,7 +138,8 @@ __device__ __forceinline__ void log_read(const Params& p, uint32_t kind, uint64_
     if (p.log != nullptr && lane == 0) {
         unsigned long long k = atomicAdd(p.log_n, 1ull);
         if (k < p.log_cap)
-            p.log[k] = ((unsigned long long)(blockIdx.x / p.strips) << 38) | ((unsigned long long)kind << 35) | id;
+            p.log[k] = ((unsigned long long)(blockIdx.x / (p.strips * p.parts)) << 38) |
+                       ((unsigned long long)kind << 35) | id;
     }
 }
 
@@ -1199,7 +1205,8 @@ __device__ void bin_frontier(Smem& sm, int32_t X0, int L, int32_t reach, int tid
 // or through the learned lookup.
 template <class V, bool kProf>
 __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src& side, int side_top, int32_t X0,
-                            int32_t Y0, int strip, int z, int32_t R, bool mask_mode, int tid) {
+                            int32_t Y0, int strip, int col0, int col_shift, int z, int32_t R, bool mask_mode,
+                            int tid) {
     int lane = tid & 31, warp = tid >> 5;
     const long long t_active = tick<kProf>();
     const int L = 23 - z;
@@ -1218,9 +1225,10 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
         int blk = 0;
         if (lane == 0) blk = atomicAdd(&sm.next_block, 1);
         blk = __shfl_sync(kFull, blk, 0);
-        if (blk >= kBlocksX * (p.rows / kBH)) break;
+        // the CTA's blocks: 2^col_shift block columns from col0, rows / 4 block rows
+        if (blk >= (p.rows / kBH) << col_shift) break;
         prof_add<kProf>(sm, kPBlocks, 1, lane);
-        int bx = blk % kBlocksX, by = blk / kBlocksX;
+        int bx = col0 / kBW + (blk & ((1 << col_shift) - 1)), by = blk >> col_shift;
         int i = bx * kBW + (lane & 7);
         int jl = by * kBH + (lane >> 3);
         int j = strip * p.rows + jl;
@@ -1351,8 +1359,8 @@ __device__ void blocks_pass(const Params& p, Smem& sm, const Src& src, const Src
 template <class V, bool kProf>
 __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* obj, const uint32_t* ids,
                       const TreeArg& st, const void* sobj, const uint32_t* sids, const LModel* m, int32_t halo,
-                      int32_t X0, int32_t Y0, int strip, int z, int32_t R, bool mask_mode, int32_t bx0, int32_t by0,
-                      int32_t bx1, int32_t by1, int tid) {
+                      int32_t X0, int32_t Y0, int strip, int col0, int col_shift, int z, int32_t R, bool mask_mode,
+                      int32_t bx0, int32_t by0, int32_t bx1, int32_t by1, int tid) {
     const long long t_cull = tick<kProf>();
     set_levels(sm, 0, t, tid);
     set_levels(sm, 1, st, tid);
@@ -1381,7 +1389,8 @@ __device__ void stage(const Params& p, Smem& sm, const TreeArg& t, const void* o
         uint16_t* const pair_scratch = reinterpret_cast<uint16_t*>(sm.fid[1 - sm.f_buf]);
         Src src{obj, ids, t.n_obj, t.nodes, sm.lvl_base[0], sm.lvl_n[0], seg_scratch, pair_scratch};
         Src side{sobj, sids, st.n_obj, st.nodes, sm.lvl_base[1], sm.lvl_n[1], seg_scratch, pair_scratch};
-        blocks_pass<V, kProf>(p, sm, src, side, side_hit ? st.top : 0, X0, Y0, strip, z, R, mask_mode, tid);
+        blocks_pass<V, kProf>(p, sm, src, side, side_hit ? st.top : 0, X0, Y0, strip, col0, col_shift, z, R, mask_mode,
+                              tid);
         __syncthreads();
         if (tid == 0) prof_since<kProf>(sm, kPBlocksCta, t_blocks, 0);
     }
@@ -1413,25 +1422,35 @@ __device__ __forceinline__ uchar4 fill_texel(const Params& p, uint32_t gx, uint3
     return p.pattern[(gy % (uint32_t)p.pat_h) * (uint32_t)p.pat_w + gx % (uint32_t)p.pat_w];
 }
 
-// Byte offset of a strip's part of a tile's output (rows x the bytes of a
-// pixel row in the mode), which holds at least rows x 32 bytes.
-__device__ __forceinline__ uint64_t strip_offset(int mode, int rows, int strip) {
-    const uint64_t row_bytes = mode == HV_MODE_MASK ? kTile / 8 : (mode == HV_MODE_COVERAGE ? kTile : 4 * kTile);
-    return (uint64_t)strip * rows * row_bytes;
+// Byte offset, in a tile's output, of pixel (c, j) (column c a multiple of 32).
+__device__ __forceinline__ uint64_t px_offset(int mode, int j, int c) {
+    if (mode == HV_MODE_MASK) return (uint64_t)j * (kTile / 8) + (uint64_t)(c >> 3);
+    return ((uint64_t)j * kTile + (uint64_t)c) * (mode == HV_MODE_COVERAGE ? 1u : 4u);
 }
 
-// The outline part of a polygon layer starts from the fill part's results:
-// a bit per pixel (centre fill), or with the anti-aliased fill a byte per
-// pixel holding the number of super-samples inside.
-__device__ void decode_fill(const uint8_t* region, Smem& sm, int rows, int tid, bool aa_bytes) {
+// The fill launch of a polygon layer hands the outline launch its results in
+// the CTA's own part of the output (which the outline overwrites): per pixel
+// row of the CTA, at the start of that row's part (cols pixels, at least
+// cols / 8 bytes in every mode), a bit per pixel (centre fill), or with the
+// anti-aliased fill a byte per pixel holding the number of super-samples
+// inside.  This reads them back into the strip's shared results.
+__device__ void decode_fill(const Params& p, const uint8_t* tile_out, Smem& sm, int strip, int col0, int cols,
+                            int tid, bool aa_bytes) {
+    const int rows = p.rows;
     if (aa_bytes) {
-        for (int k = tid; k < rows * kTile / 4; k += kThreads)
-            ((uint32_t*)sm.res)[k] = (((const uint32_t*)region)[k] & 0x07070707u) << kResFillShift;
+        const int wpr = cols / 4, wsh = __ffs(wpr) - 1;   // words per row, as a shift
+        for (int k = tid; k < rows * wpr; k += kThreads) {
+            const int jl = k >> wsh, w = k & (wpr - 1);
+            const uint32_t v = ((const uint32_t*)(tile_out + px_offset(p.mode, strip * rows + jl, col0)))[w];
+            ((uint32_t*)(sm.res + jl * kTile + col0))[w] = (v & 0x07070707u) << kResFillShift;
+        }
         return;
     }
-    for (int k = tid; k < rows * 8; k += kThreads) {
-        const uint32_t word = ((const uint32_t*)region)[k];
-        uint32_t* r4 = (uint32_t*)(sm.res + (k >> 3) * kTile + 32 * (k & 7));
+    const int wpr = cols / 32, wsh = __ffs(wpr) - 1;
+    for (int k = tid; k < rows * wpr; k += kThreads) {
+        const int jl = k >> wsh, w = k & (wpr - 1);
+        const uint32_t word = ((const uint32_t*)(tile_out + px_offset(p.mode, strip * rows + jl, col0)))[w];
+        uint32_t* r4 = (uint32_t*)(sm.res + jl * kTile + col0 + 32 * w);
 #pragma unroll
         for (int q = 0; q < 8; q++) {
             const uint32_t b = word >> (4 * q);
@@ -1444,50 +1463,53 @@ __device__ void decode_fill(const uint8_t* region, Smem& sm, int rows, int tid, 
 // The outline launch of a polygon layer encodes the strip composed over the
 // fill results: per pixel v outline samples, the fill field (centre, or the
 // anti-aliased count), a pattern texel by the global pixel coordinate.
-__device__ void encode_polygons(const Params& p, const Smem& sm, uint8_t* out, int rows, int strip,
+__device__ void encode_polygons(const Params& p, const Smem& sm, uint8_t* out, int strip, int col0, int cols,
                                 uint32_t tile, int tid) {
+    const int rows = p.rows;
     const hv_tile_req q = p.reqs[tile];
     const uint32_t gx0 = q.x * (uint32_t)kTile, gy0 = q.y * (uint32_t)kTile + (uint32_t)(strip * rows);
     if (p.mode == HV_MODE_MASK) {
-        if (tid < rows * 8) {
-            int jl = tid >> 3, w = tid & 7;
+        const int wpr = cols / 32, wsh = __ffs(wpr) - 1;
+        if (tid < rows * wpr) {
+            const int jl = tid >> wsh, c = col0 + 32 * (tid & (wpr - 1));
             uint32_t word = 0;
             for (int b = 0; b < 32; b++) {
-                const uint32_t f = sm.res[jl * kTile + 32 * w + b];
+                const uint32_t f = sm.res[jl * kTile + c + b];
                 bool filled = (f >> kResFillShift) != 0;
-                if (filled && p.pat_w) filled = fill_texel(p, gx0 + 32 * w + b, gy0 + jl).w != 0;
+                if (filled && p.pat_w) filled = fill_texel(p, gx0 + c + b, gy0 + jl).w != 0;
                 if ((f & kResCentre) || filled) word |= 1u << b;
             }
-            ((uint32_t*)out)[(strip * rows + jl) * 8 + w] = word;
+            *(uint32_t*)(out + px_offset(p.mode, strip * rows + jl, c)) = word;
         }
     } else if (p.mode == HV_MODE_COVERAGE) {
-        if (tid < rows * 16) {
-            const uint8_t* r = sm.res + tid * 16;
+        // 16 pixels (one uint4) per thread and step
+        const int upr = cols / 16, ush = __ffs(upr) - 1;
+        for (int u = tid; u < rows * upr; u += kThreads) {
+            const int jl = u >> ush, c = col0 + 16 * (u & (upr - 1));
+            const uint8_t* r = sm.res + jl * kTile + c;
             uint32_t w4[4];
             for (int k = 0; k < 4; k++) {
                 uint32_t v = 0;
                 for (int b = 0; b < 4; b++) {
                     const uint32_t f = r[4 * k + b];
                     uint32_t fill = f >> kResFillShift;
-                    if (fill && p.pat_w) {
-                        const int px = tid * 16 + 4 * k + b;
-                        if (fill_texel(p, gx0 + (px & (kTile - 1)), gy0 + px / kTile).w == 0) fill = 0;
-                    }
+                    if (fill && p.pat_w && fill_texel(p, gx0 + c + 4 * k + b, gy0 + jl).w == 0) fill = 0;
                     // anti-aliased: the fill count in bits 4-6; else bit 3 for a filled centre
-                    const uint32_t c = __popc(f & 15u) | (p.fill_aa ? fill << 4 : (fill ? 8u : 0u));
-                    v |= c << (8 * b);
+                    const uint32_t cv = __popc(f & 15u) | (p.fill_aa ? fill << 4 : (fill ? 8u : 0u));
+                    v |= cv << (8 * b);
                 }
                 w4[k] = v;
             }
-            ((uint4*)(out + (uint64_t)strip * rows * kTile))[tid] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            *(uint4*)(out + px_offset(p.mode, strip * rows + jl, c)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
         }
     } else {
-        uint4* o4 = (uint4*)(out + (uint64_t)strip * rows * kTile * 4);
-        for (int it = 0; it < rows / 4; it++) {
-            int px = (it * kThreads + tid) * 4;
+        // 4 pixels (one uint4) per thread and step
+        const int upr = cols / 4, ush = __ffs(upr) - 1;
+        for (int u = tid; u < rows * upr; u += kThreads) {
+            const int jl = u >> ush, c = col0 + 4 * (u & (upr - 1));
             uint32_t w[4];
             for (int b = 0; b < 4; b++) {
-                uint32_t f = sm.res[px + b];
+                uint32_t f = sm.res[jl * kTile + c + b];
                 uint32_t v = __popc(f & 15u);
                 uint32_t a = (255u * v + 2u) >> 2;
                 // fill count: 0..4 anti-aliased, else 4 for a filled centre
@@ -1495,7 +1517,7 @@ __device__ void encode_polygons(const Params& p, const Smem& sm, uint8_t* out, i
                 if (!p.fill_aa && fc) fc = 4;
                 uchar4 fill = p.fill;
                 if (fc && p.pat_w) {
-                    fill = fill_texel(p, gx0 + ((px + b) & (kTile - 1)), gy0 + (px + b) / kTile);
+                    fill = fill_texel(p, gx0 + c + b, gy0 + jl);
                     if (fill.w == 0) fc = 0;   // a transparent texel: not filled
                 }
                 uint32_t rgba = 0;
@@ -1518,12 +1540,14 @@ __device__ void encode_polygons(const Params& p, const Smem& sm, uint8_t* out, i
                 }
                 w[b] = rgba;
             }
-            o4[it * kThreads + tid] = make_uint4(w[0], w[1], w[2], w[3]);
+            *(uint4*)(out + px_offset(p.mode, strip * rows + jl, c)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
 
-template <int kKind, bool kProf>
+// kSplit: the launch splits strips into column parts (p.parts > 1); the
+// full-width instantiation keeps the column arithmetic compile-time constant.
+template <int kKind, bool kProf, bool kSplit>
 __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_render(const Params p) {
     __shared__ Smem sm;
     const int tid = threadIdx.x;
@@ -1532,19 +1556,22 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
         if (tid < kPN) sm.prof[tid] = 0;
     }
     const int rows = p.rows;
-    const uint32_t tile = blockIdx.x / p.strips;
-    const int strip = blockIdx.x % p.strips;
+    const int parts = kSplit ? p.parts : 1, cols = kTile / parts, col_shift = kSplit ? p.col_shift : 5;
+    // CTA -> tile, strip of rows pixel rows, part of cols pixel columns
+    const uint32_t tile = blockIdx.x / (p.strips * parts);
+    const int sp = (int)(blockIdx.x % (p.strips * parts));
+    const int strip = sp / parts, col0 = (sp % parts) * cols;
     const uint32_t n = p.n_dev ? min(*p.n_dev, p.n) : p.n;
     if (tile >= n) return;
     hv_tile_req q = p.reqs[tile];
     bool ok = q.z <= 19 && q.x < (1u << q.z) && q.y < (1u << q.z) && (p.R_units >= 0 || (q.r16 >= 1 && q.r16 <= 1024));
     if constexpr (kKind == HV_LAYER_POLYGONS)
-        decode_fill(p.out + (uint64_t)tile * p.tile_bytes + strip_offset(p.mode, rows, strip), sm, rows, tid,
+        decode_fill(p, p.out + (uint64_t)tile * p.tile_bytes, sm, strip, col0, cols, tid,
                     p.fill_aa && p.mode != HV_MODE_MASK);
     else
         for (int k = tid; k < rows * kTile / 4; k += kThreads) ((uint32_t*)sm.res)[k] = 0u;
     if (!ok) {
-        if (tid == 0 && strip == 0) atomicOr(p.status, 1u);
+        if (tid == 0 && sp == 0) atomicOr(p.status, 1u);
     }
     __syncthreads();
     if (tid == 0) prof_since<kProf>(sm, kPPrologue, t_start, 0);
@@ -1558,82 +1585,93 @@ __global__ void __launch_bounds__(kThreads, KindTraits<kKind>::kBlocksPerSM) k_r
         int32_t R = (int32_t)q.r16 << (19 - z);
         if (p.R_units >= 0) R = p.R_units;
         const int32_t off = mask_mode ? 0 : (ps >> 2);
-        // strip sample box
-        const int32_t sx0 = X0 + (ps >> 1) - off, sx1 = X0 + (kTile - 1) * ps + (ps >> 1) + off;
+        // the CTA's sample box
+        const int32_t sx0 = X0 + col0 * ps + (ps >> 1) - off, sx1 = X0 + (col0 + cols - 1) * ps + (ps >> 1) + off;
         const int32_t sy0 = Y0 + strip * rows * ps + (ps >> 1) - off;
         const int32_t sy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1) + off;
         const bool learned = p.use_learned != 0;
         // Algorithm 1 over points / segments / polygon edges
         if constexpr (kKind == HV_LAYER_POINTS)
             stage<PointLeaf, kProf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
-                             p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
+                             p.halo, X0, Y0, strip, col0, col_shift, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
         else if constexpr (kKind != kPolyFill)
             stage<SegLeaf<kKind == HV_LAYER_LINES>, kProf>(p, sm, p.tree, p.obj, nullptr, p.side, p.side_obj, p.side_ids, learned ? &p.lm : nullptr,
-                           p.halo, X0, Y0, strip, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
+                           p.halo, X0, Y0, strip, col0, col_shift, z, R, mask_mode, sx0 - R, sy0 - R, sx1 + R, sy1 + R, tid);
         // Algorithm 2 over polygon boxes and edges
         if constexpr (kKind == kPolyFill) {
-            // the strip's centres, or its super-samples
+            // the CTA's centres, or its super-samples
             const int32_t fo = (p.fill_aa && p.mode != HV_MODE_MASK) ? (ps >> 2) : 0;
-            const int32_t cx0 = X0 + (ps >> 1) - fo, cx1 = X0 + (kTile - 1) * ps + (ps >> 1) + fo;
+            const int32_t cx0 = X0 + col0 * ps + (ps >> 1) - fo, cx1 = X0 + (col0 + cols - 1) * ps + (ps >> 1) + fo;
             const int32_t cy0 = Y0 + strip * rows * ps + (ps >> 1) - fo;
             const int32_t cy1 = Y0 + (strip * rows + rows - 1) * ps + (ps >> 1) + fo;
             stage<FillLeaf, kProf>(p, sm, p.mtree, p.mbr_obj, p.mbr_ids, p.mside, p.mside_obj, p.mside_ids,
-                            learned ? &p.mlm : nullptr, p.mhalo, X0, Y0, strip, z, 0, mask_mode, cx0, cy0, cx1,
-                            cy1, tid);
+                            learned ? &p.mlm : nullptr, p.mhalo, X0, Y0, strip, col0, col_shift, z, 0, mask_mode,
+                            cx0, cy0,
+                            cx1, cy1, tid);
         }
     }
     // ---- encode the strip (Sec. 4.1 Render Tiles) ----
     const long long t_enc = tick<kProf>();
     uint8_t* out = p.out + (uint64_t)tile * p.tile_bytes;
     if constexpr (kKind == kPolyFill) {
-        // the fill results for the outline part, in the strip's own region
-        uint8_t* const region = out + strip_offset(p.mode, rows, strip);
+        // the fill results for the outline part, per pixel row at the start
+        // of the row's part of the CTA's own output (see decode_fill)
         if (p.fill_aa && p.mode != HV_MODE_MASK) {
-            for (int k = tid; k < rows * kTile / 4; k += kThreads)
-                ((uint32_t*)region)[k] = (((const uint32_t*)sm.res)[k] >> kResFillShift) & 0x07070707u;
-        } else if (tid < rows * 8) {
-            const int jl = tid >> 3, w = tid & 7;
-            uint32_t word = 0;
-            for (int b = 0; b < 32; b++)
-                if (sm.res[jl * kTile + 32 * w + b] >> kResFillShift) word |= 1u << b;
-            ((uint32_t*)region)[tid] = word;
+            const int wpr = cols / 4, wsh = __ffs(wpr) - 1;
+            for (int k = tid; k < rows * wpr; k += kThreads) {
+                const int jl = k >> wsh, w = k & (wpr - 1);
+                ((uint32_t*)(out + px_offset(p.mode, strip * rows + jl, col0)))[w] =
+                    (((const uint32_t*)(sm.res + jl * kTile + col0))[w] >> kResFillShift) & 0x07070707u;
+            }
+        } else {
+            const int wpr = cols / 32, wsh = __ffs(wpr) - 1;
+            if (tid < rows * wpr) {
+                const int jl = tid >> wsh, w = tid & (wpr - 1);
+                uint32_t word = 0;
+                for (int b = 0; b < 32; b++)
+                    if (sm.res[jl * kTile + col0 + 32 * w + b] >> kResFillShift) word |= 1u << b;
+                ((uint32_t*)(out + px_offset(p.mode, strip * rows + jl, col0)))[w] = word;
+            }
         }
     } else if constexpr (kKind == HV_LAYER_POLYGONS) {
-        encode_polygons(p, sm, out, rows, strip, tile, tid);
+        encode_polygons(p, sm, out, strip, col0, cols, tile, tid);
     } else if (p.mode == HV_MODE_MASK) {
-        // 16 rows x 8 words; word w of row j = pixels 32w .. 32w+31
-        if (tid < rows * 8) {
-            int jl = tid >> 3, w = tid & 7;
+        // word w of row j = pixels 32w .. 32w+31
+        const int wpr = cols / 32, wsh = __ffs(wpr) - 1;
+        if (tid < rows * wpr) {
+            const int jl = tid >> wsh, c = col0 + 32 * (tid & (wpr - 1));
             uint32_t word = 0;
             for (int b = 0; b < 32; b++)
-                if (sm.res[jl * kTile + 32 * w + b] & kResCentre) word |= 1u << b;
-            ((uint32_t*)out)[(strip * rows + jl) * 8 + w] = word;
+                if (sm.res[jl * kTile + c + b] & kResCentre) word |= 1u << b;
+            *(uint32_t*)(out + px_offset(p.mode, strip * rows + jl, c)) = word;
         }
     } else if (p.mode == HV_MODE_COVERAGE) {
-        // rows x 256 bytes contiguous: one uint4 (16 pixels) per thread
-        if (tid < rows * 16) {
-            const uint8_t* r = sm.res + tid * 16;
+        // one uint4 (16 pixels) per thread and step
+        const int upr = cols / 16, ush = __ffs(upr) - 1;
+        for (int u = tid; u < rows * upr; u += kThreads) {
+            const int jl = u >> ush, c = col0 + 16 * (u & (upr - 1));
+            const uint8_t* r = sm.res + jl * kTile + c;
             uint32_t w4[4];
             for (int k = 0; k < 4; k++) {
                 uint32_t v = 0;
                 for (int b = 0; b < 4; b++) v |= (uint32_t)__popc(r[4 * k + b] & 15u) << (8 * b);
                 w4[k] = v;
             }
-            ((uint4*)(out + (uint64_t)strip * rows * kTile))[tid] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            *(uint4*)(out + px_offset(p.mode, strip * rows + jl, c)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
         }
     } else {
-        // rows x 1 KB contiguous: rows / 4 rounds of one uint4 (4 pixels) per thread
-        uint4* o4 = (uint4*)(out + (uint64_t)strip * rows * kTile * 4);
-        for (int it = 0; it < rows / 4; it++) {
-            int px = (it * kThreads + tid) * 4;
+        // one uint4 (4 pixels) per thread and step
+        const int upr = cols / 4, ush = __ffs(upr) - 1;
+        for (int u = tid; u < rows * upr; u += kThreads) {
+            const int jl = u >> ush, c = col0 + 4 * (u & (upr - 1));
             uint32_t w[4];
             for (int b = 0; b < 4; b++) {
-                const uint32_t v = __popc(sm.res[px + b] & 15u);
+                const uint32_t v = __popc(sm.res[jl * kTile + c + b] & 15u);
                 const uint32_t a = (255u * v + 2u) >> 2;
                 w[b] = v ? ((uint32_t)p.line.x | ((uint32_t)p.line.y << 8) | ((uint32_t)p.line.z << 16) | (a << 24))
                          : 0u;
             }
-            o4[it * kThreads + tid] = make_uint4(w[0], w[1], w[2], w[3]);
+            *(uint4*)(out + px_offset(p.mode, strip * rows + jl, c)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
     if constexpr (kProf) {
@@ -1768,32 +1806,49 @@ int launch_render(Layer* L, const hv_tile_req* d_reqs, uint32_t n, int mode, int
     const uint64_t resident = (uint64_t)sms * per_sm;
     p.rows = (uint64_t)n * 16 >= 2 * resident ? 16 : ((uint64_t)n * 32 >= 2 * resident ? 8 : 4);
     p.strips = kTile / p.rows;
-    uint64_t grid = (uint64_t)n * p.strips;
+    // batches too small for the GPU even in 4-row strips also split each
+    // strip into 2 or 4 column parts (a CTA per 128 or 64 columns)
+    p.parts = 1;
+    if (p.rows == 4 && !prof)
+        while (p.parts < 4 && (uint64_t)n * p.strips * p.parts * 2 <= resident) p.parts *= 2;
+    p.cols = kTile / p.parts;
+    p.col_shift = p.parts == 1 ? 5 : (p.parts == 2 ? 4 : 3);
+    uint64_t grid = (uint64_t)n * p.strips * p.parts;
     if (grid > 0x7fffffffull) {
         set_error("too many tiles in one call");
         return HV_EINVAL;
     }
     if (prof) {
-        // the instrumented instantiations (phase profile); polygon layers
-        // profile their two launches (fill, outline) into two sets of counters
+        // the instrumented instantiations (phase profile, full-width strips);
+        // polygon layers profile their two launches (fill, outline) into two
+        // sets of counters
         if (L->kind == HV_LAYER_POINTS)
-            k_render<HV_LAYER_POINTS, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+            k_render<HV_LAYER_POINTS, true, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
         else if (L->kind == HV_LAYER_LINES)
-            k_render<HV_LAYER_LINES, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+            k_render<HV_LAYER_LINES, true, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
         else {
-            k_render<kPolyFill, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+            k_render<kPolyFill, true, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
             Params q = p;
             q.phases = p.phases + kPN;
-            k_render<HV_LAYER_POLYGONS, true><<<(unsigned)grid, kThreads, 0, stream>>>(q);
+            k_render<HV_LAYER_POLYGONS, true, false><<<(unsigned)grid, kThreads, 0, stream>>>(q);
+        }
+    } else if (p.parts > 1) {
+        if (L->kind == HV_LAYER_POINTS)
+            k_render<HV_LAYER_POINTS, false, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        else if (L->kind == HV_LAYER_LINES)
+            k_render<HV_LAYER_LINES, false, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        else {
+            k_render<kPolyFill, false, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+            k_render<HV_LAYER_POLYGONS, false, true><<<(unsigned)grid, kThreads, 0, stream>>>(p);
         }
     } else if (L->kind == HV_LAYER_POINTS)
-        k_render<HV_LAYER_POINTS, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        k_render<HV_LAYER_POINTS, false, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
     else if (L->kind == HV_LAYER_LINES)
-        k_render<HV_LAYER_LINES, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        k_render<HV_LAYER_LINES, false, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
     else {
         // the fill first: the outline reads its bits and writes the tile
-        k_render<kPolyFill, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
-        k_render<HV_LAYER_POLYGONS, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        k_render<kPolyFill, false, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
+        k_render<HV_LAYER_POLYGONS, false, false><<<(unsigned)grid, kThreads, 0, stream>>>(p);
     }
     HV_CUDA(cudaGetLastError());
     return HV_OK;

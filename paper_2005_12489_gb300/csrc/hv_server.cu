@@ -130,13 +130,14 @@ int launch_batch(Server* S, int k) {
     const uint64_t block_bytes = 16 + (uint64_t)S->max_batch * sizeof(hv_tile_req);
     const hv_style* style = &S->opts.style;
     if (S->opts.use_graphs) {
-        // two graphs per group: small batches launch a grid sized for a few
-        // tiles, so that each tile is split into the short strips (more CTAs
-        // per tile) that hv_render_tiles gives a small batch; larger batches
-        // launch the grid of a full batch
+        // three graphs per group: a single request and small batches launch a
+        // grid sized for one or a few tiles, so that each tile is split into
+        // the short strips and column parts (more CTAs per tile) that
+        // hv_render_tiles gives such a batch; larger batches launch the grid
+        // of a full batch
         const uint32_t small = S->max_batch < kSmallBatch ? S->max_batch : kSmallBatch;
-        const uint32_t cls = n <= small ? 0u : 1u;
-        const uint32_t n_cap = cls ? S->max_batch : small;
+        const uint32_t cls = n == 1 ? 0u : (n <= small ? 1u : 2u);
+        const uint32_t n_cap = cls == 0 ? 1u : (cls == 1 ? small : S->max_batch);
         uint64_t key = ((uint64_t)cls << 40) | ((uint64_t)r0.layer << 8) | ((uint64_t)mode << 4) | (uint64_t)index;
         auto it = sl.graphs.find(key);
         if (it == sl.graphs.end()) {
