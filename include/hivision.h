@@ -436,10 +436,11 @@ int hv_result_pool_clear(hv_result_pool* pool);
  * the worker batches the oldest request's (layer, mode) group, admitting
  * requests while the slot's output memory and max_batch allow, and launches
  * the batch on the slot's own stream (captured CUDA graphs per slot and
- * group when use_graphs is set: one for single requests and one for batches
- * of up to 8 tiles, whose grids split each tile into short strips, and for
- * a single request into column parts too, for latency; one for larger
- * batches).  Batches in different slots overlap on the device.  Completed tiles are handed out by hv_server_poll (Sec. 4.2 Result
+ * group when use_graphs is set: one for a single request on an otherwise
+ * idle device and one for batches of up to 8 tiles, whose grids split each
+ * tile into short strips, and for the single request into column parts
+ * too, for latency; one for larger batches).  Batches in different slots
+ * overlap on the device.  Completed tiles are handed out by hv_server_poll (Sec. 4.2 Result
  * Pool, without expiry). */
 typedef struct hv_server_opts {
     uint32_t max_batch;        /* tiles per batch (0 = 64, at most 4096) */

@@ -134,9 +134,15 @@ int launch_batch(Server* S, int k) {
         // grid sized for one or a few tiles, so that each tile is split into
         // the short strips and column parts (more CTAs per tile) that
         // hv_render_tiles gives such a batch; larger batches launch the grid
-        // of a full batch
+        // of a full batch.  The column parts of a single request pay off
+        // only on an idle device: with other batches in flight it takes the
+        // small-batch grid (measured: at 50,000 requests/s the parts raised
+        // p99 from 2.2 to 4.2 ms)
+        bool alone = true;
+        for (size_t j = 0; j < S->slots.size() && alone; j++)
+            if ((int)j != k && __atomic_load_n(&S->slots[j].state, __ATOMIC_RELAXED) == 1) alone = false;
         const uint32_t small = S->max_batch < kSmallBatch ? S->max_batch : kSmallBatch;
-        const uint32_t cls = n == 1 ? 0u : (n <= small ? 1u : 2u);
+        const uint32_t cls = (n == 1 && alone) ? 0u : (n <= small ? 1u : 2u);
         const uint32_t n_cap = cls == 0 ? 1u : (cls == 1 ? small : S->max_batch);
         uint64_t key = ((uint64_t)cls << 40) | ((uint64_t)r0.layer << 8) | ((uint64_t)mode << 4) | (uint64_t)index;
         auto it = sl.graphs.find(key);
