@@ -377,7 +377,9 @@ enum {
  * its phases with the SM clock and adds the warp-cycles of each phase (and a
  * few counts) to `phases` (device memory, HV_PHASE_COUNT entries, or 2 x
  * HV_PHASE_COUNT for polygon layers; the caller zeroes them).  All buffers are
- * device memory.  Used to find where the render kernel's time goes. */
+ * device memory.  The instrumented copy always renders full-width strips
+ * (no column parts for small batches).  Used to find where the render
+ * kernel's time goes. */
 int hv_render_tiles_phases(hv_layer* layer, const hv_tile_req* reqs, uint32_t n, int mode,
                            int index_kind, const hv_style* style, void* out, uint64_t out_bytes,
                            uint64_t* phases, void* stream);
