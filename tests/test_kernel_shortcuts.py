@@ -6,8 +6,9 @@ Algorithm 2's half-open ray crossing):
   a sample within R of some point of the box is in it;
 * the certain cover of a box of points (Chebyshev distance q = floor(R/sqrt 2)
   from all of the box) marks only samples that every point of the box covers;
-* squared distances of samples in a point's Chebyshev reach are exact in
-  unsigned 32-bit arithmetic when R + 2 off <= 46,340;
+* squared distances of samples in a point's Chebyshev reach, and the
+  box-to-sample gaps of the point kernel's node tests, are exact in unsigned
+  32-bit arithmetic when R + 2 off <= 46,340;
 * the crossed columns of an edge per pixel row, found by a three-step search
   over exact products, are the columns whose centre the edge crosses
   strictly to the right (half-open in y).
@@ -288,3 +289,43 @@ def test_planted_mistakes_are_caught():
         if counted_with_ge != bin((m >> (8 * r)) & 0xFF).count("1"):
             bad_tie += 1
     assert bad_tie > 0
+
+
+def test_narrow_box_reach_equals_the_exact_gap_test():
+    """The node and frontier reach test of the point kernel in unsigned 32-bit
+    arithmetic: for the lanes in a box's Chebyshev reach, gaps are at most
+    R + 2 off, so under R + 2 off <= 46,340 the 32-bit test equals the exact
+    box-to-sample test (Algorithm 1's distance <= R, to the nearest point of
+    the box)."""
+    rng = np.random.default_rng(16)
+    M = (1 << 32) - 1
+    checked = 0
+    for _ in range(3000):
+        z = int(rng.integers(9, 20))
+        L = 23 - z
+        ps = 1 << L
+        off = (ps >> 2) if rng.random() < 0.75 else 0
+        R = int(rng.integers(0, 46340 - 2 * off + 1))
+        bx0 = int(rng.integers(-HALF, HALF - 8 * ps)) // ps * ps + ps // 2
+        by0 = int(rng.integers(-HALF, HALF - 4 * ps)) // ps * ps + ps // 2
+        x0, y0, x1, y1 = _box_near(rng, bx0, by0, ps, R, off)
+        cand = rect_lanes(bx0, by0, L, R + off, x0, y0, x1, y1)
+        ax = max(min(x0 - bx0, HALF), -HALF)
+        bx = max(min(x1 - bx0, HALF), -HALF)
+        ay = max(min(y0 - by0, HALF), -HALF)
+        by = max(min(y1 - by0, HALF), -HALF)
+        for lane in range(32):
+            if not (cand >> lane) & 1:
+                continue
+            sx, sy = (lane & 7) << L, (lane >> 3) << L
+            for k in range(4 if off else 1):
+                px = sx + (off if k & 1 else -off)
+                py = sy + (off if k & 2 else -off)
+                gx = max(ax - px, px - bx, 0)
+                gy = max(ay - py, py - by, 0)
+                assert gx <= R + 2 * off and gy <= R + 2 * off
+                narrow = ((gx * gx + gy * gy) & M) <= ((R * R) & M)
+                exact = _box_dist2(x0, y0, x1, y1, bx0 + px, by0 + py) <= R * R
+                assert narrow == exact, (L, off, R, (x0, y0, x1, y1), lane, k)
+                checked += 1
+    assert checked > 1000
