@@ -11,7 +11,9 @@ Algorithm 2's half-open ray crossing):
   32-bit arithmetic when R + 2 off <= 46,340;
 * the crossed columns of an edge per pixel row, found by a three-step search
   over exact products, are the columns whose centre the edge crosses
-  strictly to the right (half-open in y).
+  strictly to the right (half-open in y);
+* a segment leaf's staging of (piece, pixel) pairs takes every pair exactly
+  once over its rounds.
 
 Each model follows the kernel's steps (shifts by the pixel size, clamps to
 +-2^30, 32-bit wrap-around) in Python integers.  No GPU is needed.
@@ -329,3 +331,45 @@ def test_narrow_box_reach_equals_the_exact_gap_test():
                 assert narrow == exact, (L, off, R, (x0, y0, x1, y1), lane, k)
                 checked += 1
     assert checked > 1000
+
+
+def stage_pairs(pm, cap=128):
+    """The segment leaf's staging of (piece, pixel) pairs: lane p's pairs are
+    numbered from the exclusive prefix sum of the lanes' pixel counts; each
+    round writes the pairs numbered [w0, w0 + cap) (unsigned wrap-around
+    skips the earlier ones) and the warp then takes them in turn."""
+    cnt = [bin(m).count("1") for m in pm]
+    first = [sum(cnt[:p]) for p in range(32)]
+    total = sum(cnt)
+    rounds = []
+    w0 = 0
+    while w0 < total:
+        slots = [None] * cap
+        for p in range(32):
+            m, g = pm[p], (first[p] - w0) & 0xFFFFFFFF
+            while m:
+                low = m & -m
+                lane = low.bit_length() - 1
+                m &= m - 1
+                if g < cap:
+                    assert slots[g] is None
+                    slots[g] = (p << 5) | lane
+                g = (g + 1) & 0xFFFFFFFF
+        n = min(total - w0, cap)
+        assert all(v is not None for v in slots[:n]) and all(v is None for v in slots[n:])
+        rounds.append(slots[:n])
+        w0 += cap
+    return rounds
+
+
+def test_pair_staging_takes_every_pair_once():
+    """Up to 32 x 32 pairs per leaf, so up to 8 rounds of 128."""
+    rng = np.random.default_rng(17)
+    for _ in range(500):
+        density = rng.choice([0.02, 0.2, 0.5, 1.0])
+        pm = [int(sum(1 << b for b in range(32) if rng.random() < density)) for _ in range(32)]
+        rounds = stage_pairs(pm)
+        got = sorted(e for r in rounds for e in r)
+        want = sorted((p << 5) | b for p in range(32) for b in range(32) if (pm[p] >> b) & 1)
+        assert got == want
+        assert len(rounds) == -(-len(want) // 128)
