@@ -152,3 +152,34 @@ def test_polygon_outlines_at_the_radius(ctx):
             assert bad.size == 0, "mode %d: %d tiles differ, first %s" % (mode, bad.size, reqs[bad[0]])
     finally:
         hv.hv_layer_free(L)
+
+
+def test_leaves_with_more_pairs_than_one_round(ctx):
+    """Hundreds of long segments through the same pixel blocks at a 64 px
+    half-width: a leaf's 32 pieces each reach every pixel of a block, up to
+    1,024 (piece, pixel) pairs, staged and tested in rounds of 128; every
+    tile equals the oracle's."""
+    z, tx, ty = 16, 30000, 25000
+    rng = np.random.default_rng(7)
+    segs = []
+    for k in range(400):
+        cx, cy = centre(z, tx, ty, int(rng.integers(0, 64)), int(rng.integers(0, 64)))
+        ang = rng.uniform(0, np.pi)
+        L_ = int(rng.integers(1 << 12, 1 << 22))
+        dx, dy = int(L_ * np.cos(ang)), int(L_ * np.sin(ang))
+        segs.append(tuple(_clip(v) for v in (cx - dx, cy - dy, cx + dx, cy + dy)))
+    xy = np.array([[a, b] for s in segs for a, b in ((s[0], s[1]), (s[2], s[3]))], dtype=np.int32)
+    off = np.arange(0, 2 * len(segs) + 1, 2, dtype=np.uint64)
+    reqs = np.array([[z, tx, ty, 1024], [z, tx, ty, 512], [z, tx, ty, 96], [z - 1, tx // 2, ty // 2, 1024],
+                     [z, tx + 1, ty, 1024]],
+                    dtype=np.uint32)
+    L = hv.hv_layer_load_linestrings(ctx, xy, off)
+    hv.hv_layer_build_index(L)
+    try:
+        for mode in MODES:
+            got = _render(L, reqs, mode)
+            ref = oracle_par.render(lambda r: oracle.render_lines(xy, off, r, mode, STYLE_T), reqs)
+            bad = np.nonzero((got != ref).any(axis=1))[0]
+            assert bad.size == 0, "mode %d: %d tiles differ, first %s" % (mode, bad.size, reqs[bad[0]])
+    finally:
+        hv.hv_layer_free(L)
